@@ -1,0 +1,139 @@
+/*
+ * gecc.h -- C ABI of the GB300 batched elliptic-curve library.
+ *
+ * The library implements the data-parallel hot path of gECC (arXiv 2501.03245):
+ * Montgomery multiplication on 32-bit limbs (Section 4.1, Algorithm 2), batch
+ * inversion by Montgomery's trick with per-CTA gather-apply-scatter (Sections
+ * 2.2.1 and 3.2), batched affine point addition / doubling (Section 3.3,
+ * Eqn 2-3), and on top of them ECDSA verification (Section 5.2: one fixed-point
+ * plus one unknown-point multiplication) and Pippenger multi-scalar
+ * multiplication.
+ *
+ * Conventions shared by every entry point
+ *   - Return value: ECC_OK (0) or a negative ECC_E* code; the matching message
+ *     is available from ecc_last_error() (thread-local, valid until the next
+ *     call on the same thread).  Argument errors are reported synchronously;
+ *     CUDA launch errors too.  Kernels run asynchronously on `stream` (a
+ *     cudaStream_t; NULL = the legacy default stream).
+ *   - n = 0 returns ECC_OK and does no work.
+ *   - Memory: unless an entry point says otherwise, every array is caller-owned
+ *     and may be device memory (results are ready when `stream` reaches the
+ *     end of the call) or host memory (pageable or pinned; the call then
+ *     stages through device memory and returns after the results are written
+ *     back, i.e. it is synchronous).  The library owns only its internal
+ *     workspace (stream-ordered allocations released at the end of each call)
+ *     and the per-device fixed-base tables (built on first use of a curve and
+ *     kept until process exit).  The first call that needs a curve's table
+ *     builds it synchronously; do that call before any stream capture.
+ *   - Field elements: little-endian 32-bit limbs, canonical (< modulus).  A
+ *     base-field element of BN254 / secp256k1 / P-256 has 8 limbs, of
+ *     BLS12-381 12 limbs (ecc_limbs()).  Scalars are always 8 limbs.
+ *   - Affine points: x limbs then y limbs (2 * ecc_limbs() words per point);
+ *     the point at infinity O is written (0, 0), which is on none of the
+ *     supported curves (b != 0).
+ *   - Pointers must be 4-byte aligned.
+ */
+#ifndef GECC_H
+#define GECC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ECC_SECP256K1 = 0,    /* SEC 2 secp256k1: a = 0, b = 7 */
+  ECC_P256 = 1,         /* NIST P-256 (secp256r1): a = -3 */
+  ECC_BN254 = 2,        /* BN254 G1: a = 0, b = 3 */
+  ECC_BLS12_381 = 3     /* BLS12-381 G1: a = 0, b = 4, 381-bit base field */
+} ecc_curve_t;
+
+enum {
+  ECC_OK = 0,
+  ECC_EINVAL = -1,       /* bad argument (curve, NULL pointer, alignment, size) */
+  ECC_EUNSUPPORTED = -2, /* operation not offered for this curve */
+  ECC_ENOMEM = -3,       /* device workspace allocation failed */
+  ECC_ECUDA = -4,        /* CUDA runtime error (message has the CUDA string) */
+  ECC_ETIMEOUT = -5      /* a bounded device wait gave up */
+};
+
+/* Which field an ecc_fp_* call works in. */
+enum { ECC_FIELD_BASE = 0, ECC_FIELD_SCALAR = 1 };
+
+/* Thread-local message for the last non-OK return ("" if none). */
+const char* ecc_last_error(void);
+
+/* Library version string. */
+const char* ecc_version(void);
+
+/* Limbs of a base-field element (8 or 12), or ECC_EINVAL. */
+int ecc_limbs(ecc_curve_t curve);
+
+/* ---------------------------------------------------------------- field layer
+ * out[i] = a[i] * b[i] mod q (Algorithm 2, Section 2.2: Montgomery
+ * multiplication; inputs are converted into Montgomery form and back).
+ * field: ECC_FIELD_BASE (q = p) or ECC_FIELD_SCALAR (q = group order n).
+ * a, b, out: n rows of L limbs (L = ecc_limbs() for the base field, 8 for the
+ * scalar field); inputs must be canonical. */
+int ecc_fp_mul(ecc_curve_t curve, int field, size_t n, const uint32_t* a, const uint32_t* b,
+               uint32_t* out, void* stream);
+
+/* out[i] = a[i] + b[i] mod q, and a[i] - b[i] mod q (Section 2.2 modadd). */
+int ecc_fp_add(ecc_curve_t curve, int field, size_t n, const uint32_t* a, const uint32_t* b,
+               uint32_t* out, void* stream);
+int ecc_fp_sub(ecc_curve_t curve, int field, size_t n, const uint32_t* a, const uint32_t* b,
+               uint32_t* out, void* stream);
+
+/* out[i] = a[i]^-1 mod q, one Fermat inversion a^(q-2) per element
+ * (Section 2.2 modinv); a[i] = 0 gives 0. */
+int ecc_fp_inv(ecc_curve_t curve, int field, size_t n, const uint32_t* a, uint32_t* out,
+               void* stream);
+
+/* out[i] = a[i]^-1 mod q for the whole array by Montgomery's trick
+ * (Section 2.2.1) with the gather-apply-scatter workflow of Section 3.2: one
+ * modular inversion per CTA.  Zero elements give 0 and do not disturb the
+ * others. */
+int ecc_fp_inv_batch(ecc_curve_t curve, int field, size_t n, const uint32_t* a, uint32_t* out,
+                     void* stream);
+
+/* ---------------------------------------------------------------- EC operators
+ * out[i] = p[i] + q[i] (batched affine PADD, Section 3.3, Eqn 2-3; PDBL when
+ * p[i] = q[i]; O and p[i] = -q[i] follow the group law).  Points must be on the
+ * curve (not checked). */
+int ecc_point_add_batch(ecc_curve_t curve, size_t n, const uint32_t* p, const uint32_t* q,
+                        uint32_t* out, void* stream);
+
+/* out[i] = 2 p[i] (batched affine PDBL, Section 2.1.1). */
+int ecc_point_dbl_batch(ecc_curve_t curve, size_t n, const uint32_t* p, uint32_t* out,
+                        void* stream);
+
+/* ---------------------------------------------------------------- ECDSA
+ * Batched ECDSA verification (Section 5.2; SEC 1 section 4.1.4).
+ * curve: ECC_SECP256K1 or ECC_P256 (others: ECC_EUNSUPPORTED).
+ * hash, r, s: n x 32 bytes, big-endian integers (the hash is used as e without
+ * truncation: both group orders are 256-bit).
+ * pubkey: n x 64 bytes, x || y big-endian, uncompressed, no 0x04 prefix.
+ * ok_out: n bytes, 1 = valid signature, 0 = invalid.  Malformed input
+ * (r or s outside [1, n-1], Q off the curve or not canonical, Q = (0, 0)) gives
+ * 0, not an error. */
+int ecc_verify_batch(ecc_curve_t curve, size_t n, const uint8_t* hash, const uint8_t* r,
+                     const uint8_t* s, const uint8_t* pubkey, uint8_t* ok_out, void* stream);
+
+/* ---------------------------------------------------------------- benchmarks
+ * Integer multiply-add issue-rate probe (the microbenchmark method of
+ * Section 4.1, Table 2): each of `threads` threads runs `iters` iterations of
+ * `chains` independent mad.lo/madc.hi (IMAD.WIDE-class) carry chains.  Writes a
+ * data-dependent checksum per thread to sink (device, threads words) so the
+ * work cannot be elided.  Time it with CUDA events around the call. */
+int ecc_bench_imad(size_t threads, int iters, uint32_t* sink, void* stream);
+
+/* Montgomery multiplications in registers: each thread runs `iters` rounds of
+ * 4 independent mont_mul chains of the curve's base field.  sink as above. */
+int ecc_bench_modmul(ecc_curve_t curve, size_t threads, int iters, uint32_t* sink, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GECC_H */

@@ -1,0 +1,282 @@
+// C ABI (include/gecc.h): argument checks, host-memory staging, error strings.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/gecc.h"
+#include "internal.h"
+
+namespace ecc {
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int ok() {
+  g_err[0] = 0;
+  return ECC_OK;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  if (e == cudaErrorMemoryAllocation) return fail(ECC_ENOMEM, "%s: %s", where, cudaGetErrorString(e));
+  return fail(ECC_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+bool host_memory(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
+}
+
+bool aligned4(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 3u) == 0; }
+
+// Device view of a caller array: the array itself when it is device memory,
+// otherwise a stream-ordered device copy (inputs copied in; outputs copied back
+// by flush()).
+struct Arg {
+  const void* user;
+  void* dev = nullptr;
+  size_t bytes;
+  bool staged = false;
+  Scratch buf;
+  Arg(const void* p, size_t b) : user(p), bytes(b) {}
+  cudaError_t in(cudaStream_t st) {
+    if (!host_memory(user)) {
+      dev = const_cast<void*>(user);
+      return cudaSuccess;
+    }
+    staged = true;
+    cudaError_t e = buf.alloc(bytes, st);
+    if (e != cudaSuccess) return e;
+    dev = buf.ptr;
+    return cudaMemcpyAsync(dev, user, bytes, cudaMemcpyHostToDevice, st);
+  }
+  cudaError_t out(cudaStream_t st) {
+    if (!host_memory(user)) {
+      dev = const_cast<void*>(user);
+      return cudaSuccess;
+    }
+    staged = true;
+    cudaError_t e = buf.alloc(bytes, st);
+    dev = buf.ptr;
+    return e;
+  }
+  cudaError_t flush(cudaStream_t st) {
+    if (!staged) return cudaSuccess;
+    return cudaMemcpyAsync(const_cast<void*>(user), dev, bytes, cudaMemcpyDeviceToHost, st);
+  }
+};
+
+bool valid_curve(int c) { return c >= 0 && c <= 3; }
+
+// Runs `body` with device views of the inputs/outputs; synchronises when any
+// of them was staged from host memory.
+template <class Body>
+int with_args(const char* name, cudaStream_t st, std::vector<Arg*> ins, std::vector<Arg*> outs,
+              Body body) {
+  for (Arg* a : ins) {
+    cudaError_t e = a->in(st);
+    if (e != cudaSuccess) return cuda_fail(e, name);
+  }
+  for (Arg* a : outs) {
+    cudaError_t e = a->out(st);
+    if (e != cudaSuccess) return cuda_fail(e, name);
+  }
+  cudaError_t e = body();
+  if (e != cudaSuccess) return cuda_fail(e, name);
+  bool staged = false;
+  for (Arg* a : ins) staged |= a->staged;
+  for (Arg* a : outs) {
+    staged |= a->staged;
+    e = a->flush(st);
+    if (e != cudaSuccess) return cuda_fail(e, name);
+  }
+  if (staged) {
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, name);
+  }
+  return ok();
+}
+
+}  // namespace
+
+cudaError_t Scratch::alloc(size_t b, cudaStream_t s) {
+  if (ptr) cudaFreeAsync(ptr, st);
+  ptr = nullptr;
+  st = s;
+  bytes = b;
+  if (b == 0) b = 16;
+  static bool pool_set = false;
+  if (!pool_set) {
+    // keep freed stream-ordered memory cached in the pool between calls
+    int dev = 0;
+    cudaMemPool_t pool;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    pool_set = true;
+  }
+  return cudaMallocAsync(&ptr, b, s);
+}
+
+int device_sm_count() {
+  static int cache[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return 1;
+  if (!cache[dev]) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    cache[dev] = v > 0 ? v : 1;
+  }
+  return cache[dev];
+}
+
+std::string cuda_msg(cudaError_t e) { return cudaGetErrorString(e); }
+
+}  // namespace ecc
+
+using namespace ecc;
+
+extern "C" {
+
+const char* ecc_last_error(void) { return g_err; }
+
+const char* ecc_version(void) { return "gecc-gb300 0.1"; }
+
+int ecc_limbs(ecc_curve_t curve) {
+  if (!valid_curve(curve)) return fail(ECC_EINVAL, "ecc_limbs: unknown curve %d", (int)curve);
+  return field_limbs(curve, 0);
+}
+
+static int fp_binary(const char* name, int op, ecc_curve_t curve, int field, size_t n,
+                     const uint32_t* a, const uint32_t* b, uint32_t* out, void* stream) {
+  if (!valid_curve(curve)) return fail(ECC_EINVAL, "%s: unknown curve %d", name, (int)curve);
+  if (field != 0 && field != 1) return fail(ECC_EINVAL, "%s: field must be 0 or 1", name);
+  if (n == 0) return ok();
+  if (!a || !out || (op < 3 && !b)) return fail(ECC_EINVAL, "%s: NULL pointer", name);
+  if (!aligned4(a) || !aligned4(out) || (b && !aligned4(b)))
+    return fail(ECC_EINVAL, "%s: pointers must be 4-byte aligned", name);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t bytes = n * field_limbs(curve, field) * 4;
+  Arg A(a, bytes), B(b ? b : a, bytes), O(out, bytes);
+  std::vector<Arg*> ins{&A};
+  if (op < 3) ins.push_back(&B);
+  return with_args(name, st, ins, {&O}, [&]() {
+    const uint32_t* da = static_cast<const uint32_t*>(A.dev);
+    const uint32_t* db = static_cast<const uint32_t*>(B.dev);
+    uint32_t* dout = static_cast<uint32_t*>(O.dev);
+    switch (op) {
+      case 0: return launch_fe_mul(curve, field, n, da, db, dout, st);
+      case 1: return launch_fe_addsub(curve, field, n, da, db, dout, 0, st);
+      case 2: return launch_fe_addsub(curve, field, n, da, db, dout, 1, st);
+      case 3: return launch_fe_inv(curve, field, n, da, dout, st);
+      default: return launch_fe_inv_batch(curve, field, n, da, dout, st);
+    }
+  });
+}
+
+int ecc_fp_mul(ecc_curve_t curve, int field, size_t n, const uint32_t* a, const uint32_t* b,
+               uint32_t* out, void* stream) {
+  return fp_binary("ecc_fp_mul", 0, curve, field, n, a, b, out, stream);
+}
+
+int ecc_fp_add(ecc_curve_t curve, int field, size_t n, const uint32_t* a, const uint32_t* b,
+               uint32_t* out, void* stream) {
+  return fp_binary("ecc_fp_add", 1, curve, field, n, a, b, out, stream);
+}
+
+int ecc_fp_sub(ecc_curve_t curve, int field, size_t n, const uint32_t* a, const uint32_t* b,
+               uint32_t* out, void* stream) {
+  return fp_binary("ecc_fp_sub", 2, curve, field, n, a, b, out, stream);
+}
+
+int ecc_fp_inv(ecc_curve_t curve, int field, size_t n, const uint32_t* a, uint32_t* out,
+               void* stream) {
+  return fp_binary("ecc_fp_inv", 3, curve, field, n, a, nullptr, out, stream);
+}
+
+int ecc_fp_inv_batch(ecc_curve_t curve, int field, size_t n, const uint32_t* a, uint32_t* out,
+                     void* stream) {
+  return fp_binary("ecc_fp_inv_batch", 4, curve, field, n, a, nullptr, out, stream);
+}
+
+static int point_op(const char* name, ecc_curve_t curve, size_t n, const uint32_t* p,
+                    const uint32_t* q, uint32_t* out, int dbl, void* stream) {
+  if (!valid_curve(curve)) return fail(ECC_EINVAL, "%s: unknown curve %d", name, (int)curve);
+  if (n == 0) return ok();
+  if (!p || !out || (!dbl && !q)) return fail(ECC_EINVAL, "%s: NULL pointer", name);
+  if (!aligned4(p) || !aligned4(out) || (q && !aligned4(q)))
+    return fail(ECC_EINVAL, "%s: pointers must be 4-byte aligned", name);
+  if (n > (size_t)1 << 30) return fail(ECC_EINVAL, "%s: n > 2^30", name);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t bytes = n * 2 * field_limbs(curve, 0) * 4;
+  Arg P(p, bytes), Q(q ? q : p, bytes), O(out, bytes);
+  std::vector<Arg*> ins{&P};
+  if (!dbl) ins.push_back(&Q);
+  return with_args(name, st, ins, {&O}, [&]() {
+    return launch_point_add(curve, n, static_cast<const uint32_t*>(P.dev),
+                            static_cast<const uint32_t*>(Q.dev), static_cast<uint32_t*>(O.dev),
+                            dbl, st);
+  });
+}
+
+int ecc_point_add_batch(ecc_curve_t curve, size_t n, const uint32_t* p, const uint32_t* q,
+                        uint32_t* out, void* stream) {
+  return point_op("ecc_point_add_batch", curve, n, p, q, out, 0, stream);
+}
+
+int ecc_point_dbl_batch(ecc_curve_t curve, size_t n, const uint32_t* p, uint32_t* out,
+                        void* stream) {
+  return point_op("ecc_point_dbl_batch", curve, n, p, nullptr, out, 1, stream);
+}
+
+int ecc_verify_batch(ecc_curve_t curve, size_t n, const uint8_t* hash, const uint8_t* r,
+                     const uint8_t* s, const uint8_t* pubkey, uint8_t* ok_out, void* stream) {
+  const char* name = "ecc_verify_batch";
+  if (!valid_curve(curve)) return fail(ECC_EINVAL, "%s: unknown curve %d", name, (int)curve);
+  if (curve != ECC_SECP256K1 && curve != ECC_P256)
+    return fail(ECC_EUNSUPPORTED, "%s: ECDSA is offered on secp256k1 and P-256", name);
+  if (n == 0) return ok();
+  if (!hash || !r || !s || !pubkey || !ok_out) return fail(ECC_EINVAL, "%s: NULL pointer", name);
+  if (!aligned4(hash) || !aligned4(r) || !aligned4(s) || !aligned4(pubkey))
+    return fail(ECC_EINVAL, "%s: input pointers must be 4-byte aligned", name);
+  if (n > (size_t)1 << 26) return fail(ECC_EINVAL, "%s: n > 2^26", name);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Arg H(hash, 32 * n), R(r, 32 * n), S(s, 32 * n), Q(pubkey, 64 * n), O(ok_out, n);
+  return with_args(name, st, {&H, &R, &S, &Q}, {&O}, [&]() {
+    return launch_verify(curve, n, static_cast<const uint8_t*>(H.dev),
+                         static_cast<const uint8_t*>(R.dev), static_cast<const uint8_t*>(S.dev),
+                         static_cast<const uint8_t*>(Q.dev), static_cast<uint8_t*>(O.dev), st);
+  });
+}
+
+int ecc_bench_imad(size_t threads, int iters, uint32_t* sink, void* stream) {
+  if (threads == 0 || iters < 0 || !sink) return fail(ECC_EINVAL, "ecc_bench_imad: bad argument");
+  cudaError_t e = launch_bench_imad(threads, iters, sink, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "ecc_bench_imad");
+  return ok();
+}
+
+int ecc_bench_modmul(ecc_curve_t curve, size_t threads, int iters, uint32_t* sink, void* stream) {
+  if (!valid_curve(curve)) return fail(ECC_EINVAL, "ecc_bench_modmul: unknown curve");
+  if (threads == 0 || iters < 0 || !sink) return fail(ECC_EINVAL, "ecc_bench_modmul: bad argument");
+  cudaError_t e = launch_bench_modmul(curve, threads, iters, sink, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "ecc_bench_modmul");
+  return ok();
+}
+
+}  // extern "C"

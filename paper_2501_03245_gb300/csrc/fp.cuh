@@ -1,0 +1,263 @@
+// Prime-field arithmetic on 32-bit limbs (modular arithmetic layer, Section 4).
+//
+// Elements are N little-endian 32-bit limbs (N even: 8 for 254/256-bit fields,
+// 12 for the 381-bit field) held in registers, in Montgomery form a*R mod q with
+// R = 2^(32N), canonical in [0, q).  A field is a traits class F with
+//   N, QINV = -q^-1 mod 2^32, p(i), r2(i) = R^2 mod q, one(i) = R mod q,
+//   pm2(i) = q - 2.
+//
+// mont_mul is Montgomery multiplication (Algorithm 2) with the operand-scanning
+// order interleaved row by row.  Each row A*b_i is split into an "even" chain
+// (a_j b_i, j even) and an "odd" chain (a_j b_i, j odd), the mad_n carry chains
+// of Section 4.1: within one chain the 64-bit products sit on disjoint word
+// pairs, so one chain of alternating mad.lo / mad.hi links covers the row with a
+// single carry.  The running value is kept as T = c + 2^32 d with c collecting
+// the even chains and d the odd chains; the reduction row u*q (u = T_0 * QINV)
+// is split the same way.  Dividing T by 2^32 then only renames registers
+// (d becomes the new c, the upper words of c the new d) plus one add for word 0,
+// whose carry enters the next odd chain as its carry-in -- so the count is
+// 2N^2 + N multiply-adds (136 IMAD.WIDE-class for N = 8), as Section 4.1
+// derives, and only ~4N extra adds.  The final value is < 2q and is brought
+// into [0, q) with one conditional subtraction.
+#pragma once
+#include <cstdint>
+
+#include "ptx.cuh"
+
+namespace ecc {
+
+template <class F>
+struct Fe {
+  uint32_t v[F::N];
+};
+
+template <class F>
+ECC_DEV void fe_copy(uint32_t* r, const uint32_t* a) {
+#pragma unroll
+  for (int i = 0; i < F::N; ++i) r[i] = a[i];
+}
+
+template <class F>
+ECC_DEV void fe_set_one(uint32_t* r) {
+#pragma unroll
+  for (int i = 0; i < F::N; ++i) r[i] = F::one(i);
+}
+
+template <class F>
+ECC_DEV void fe_set_zero(uint32_t* r) {
+#pragma unroll
+  for (int i = 0; i < F::N; ++i) r[i] = 0;
+}
+
+template <class F>
+ECC_DEV bool fe_is_zero(const uint32_t* a) {
+  uint32_t acc = 0;
+#pragma unroll
+  for (int i = 0; i < F::N; ++i) acc |= a[i];
+  return acc == 0;
+}
+
+template <class F>
+ECC_DEV bool fe_eq(const uint32_t* a, const uint32_t* b) {
+  uint32_t acc = 0;
+#pragma unroll
+  for (int i = 0; i < F::N; ++i) acc |= a[i] ^ b[i];
+  return acc == 0;
+}
+
+template <class F>
+ECC_DEV bool fe_is_one(const uint32_t* a) {
+  uint32_t acc = 0;
+#pragma unroll
+  for (int i = 0; i < F::N; ++i) acc |= a[i] ^ F::one(i);
+  return acc == 0;
+}
+
+// r = cond ? a : b
+template <class F>
+ECC_DEV void fe_select(uint32_t* r, bool cond, const uint32_t* a, const uint32_t* b) {
+#pragma unroll
+  for (int i = 0; i < F::N; ++i) r[i] = cond ? a[i] : b[i];
+}
+
+// a < q as plain integers (used to validate canonical inputs)
+template <class F>
+ECC_DEV bool fe_lt_modulus(const uint32_t* a) {
+  uint32_t t = ptx::sub_cc(a[0], F::p(0));
+#pragma unroll
+  for (int i = 1; i < F::N; ++i) t = ptx::subc_cc(a[i], F::p(i));
+  uint32_t borrow = ptx::subc(0, 0);
+  (void)t;
+  return borrow != 0;
+}
+
+// r = a + b mod q
+template <class F>
+ECC_DEV void fe_add(uint32_t* r, const uint32_t* a, const uint32_t* b) {
+  constexpr int N = F::N;
+  uint32_t t[N], s[N];
+  t[0] = ptx::add_cc(a[0], b[0]);
+#pragma unroll
+  for (int i = 1; i < N; ++i) t[i] = ptx::addc_cc(a[i], b[i]);
+  uint32_t top = ptx::addc(0, 0);
+  s[0] = ptx::sub_cc(t[0], F::p(0));
+#pragma unroll
+  for (int i = 1; i < N; ++i) s[i] = ptx::subc_cc(t[i], F::p(i));
+  top = ptx::subc(top, 0);  // 0xffffffff iff a + b < q
+#pragma unroll
+  for (int i = 0; i < N; ++i) r[i] = top ? t[i] : s[i];
+}
+
+// r = a - b mod q
+template <class F>
+ECC_DEV void fe_sub(uint32_t* r, const uint32_t* a, const uint32_t* b) {
+  constexpr int N = F::N;
+  uint32_t t[N];
+  t[0] = ptx::sub_cc(a[0], b[0]);
+#pragma unroll
+  for (int i = 1; i < N; ++i) t[i] = ptx::subc_cc(a[i], b[i]);
+  uint32_t mask = ptx::subc(0, 0);  // 0xffffffff iff a < b
+  r[0] = ptx::add_cc(t[0], F::p(0) & mask);
+#pragma unroll
+  for (int i = 1; i < N - 1; ++i) r[i] = ptx::addc_cc(t[i], F::p(i) & mask);
+  r[N - 1] = ptx::addc(t[N - 1], F::p(N - 1) & mask);
+}
+
+template <class F>
+ECC_DEV void fe_neg(uint32_t* r, const uint32_t* a) {
+  uint32_t z[F::N];
+  fe_set_zero<F>(z);
+  fe_sub<F>(r, z, a);
+}
+
+// Montgomery product r = a * b * R^-1 mod q (r may alias a or b).
+template <class F>
+ECC_DEV void mont_mul(uint32_t* r, const uint32_t* a, const uint32_t* b) {
+  constexpr int N = F::N;
+  static_assert(N % 2 == 0, "even limb count");
+  uint32_t c[N + 1], d[N + 1];
+#pragma unroll
+  for (int i = 0; i < N + 1; ++i) {
+    c[i] = 0;
+    d[i] = 0;
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const uint32_t bi = b[i];
+    if (i == 0) {
+      // odd chain: d[j-1], d[j] += a_j * b_0 for odd j
+      d[0] = ptx::mad_lo_cc(a[1], bi, d[0]);
+      d[1] = ptx::madc_hi_cc(a[1], bi, d[1]);
+    } else {
+      // T /= 2^32: new c = (d0 + c1, d1, .., dN), new d = (c2, .., cN, 0, 0);
+      // the carry of d0 + c1 (word 1) is the carry-in of the odd chain.
+      uint32_t nc0 = ptx::add_cc(d[0], c[1]);
+#pragma unroll
+      for (int k = 0; k < N - 1; ++k) {
+        uint32_t t = d[k + 1];
+        d[k] = c[k + 2];
+        c[k + 1] = t;
+      }
+      c[N] = d[N];
+      c[0] = nc0;
+      d[N - 1] = 0;
+      d[N] = 0;
+      d[0] = ptx::madc_lo_cc(a[1], bi, d[0]);
+      d[1] = ptx::madc_hi_cc(a[1], bi, d[1]);
+    }
+#pragma unroll
+    for (int j = 3; j < N; j += 2) {
+      d[j - 1] = ptx::madc_lo_cc(a[j], bi, d[j - 1]);
+      d[j] = ptx::madc_hi_cc(a[j], bi, d[j]);
+    }
+    d[N] = ptx::addc(d[N], 0);
+    // even chain: c[j], c[j+1] += a_j * b_i for even j
+    c[0] = ptx::mad_lo_cc(a[0], bi, c[0]);
+    c[1] = ptx::madc_hi_cc(a[0], bi, c[1]);
+#pragma unroll
+    for (int j = 2; j < N; j += 2) {
+      c[j] = ptx::madc_lo_cc(a[j], bi, c[j]);
+      c[j + 1] = ptx::madc_hi_cc(a[j], bi, c[j + 1]);
+    }
+    c[N] = ptx::addc(c[N], 0);
+    // reduction row: u = T_0 * QINV, T += u * q (even and odd chains)
+    const uint32_t u = c[0] * F::QINV;
+    c[0] = ptx::mad_lo_cc(u, F::p(0), c[0]);
+    c[1] = ptx::madc_hi_cc(u, F::p(0), c[1]);
+#pragma unroll
+    for (int j = 2; j < N; j += 2) {
+      c[j] = ptx::madc_lo_cc(u, F::p(j), c[j]);
+      c[j + 1] = ptx::madc_hi_cc(u, F::p(j), c[j + 1]);
+    }
+    c[N] = ptx::addc(c[N], 0);
+    d[0] = ptx::mad_lo_cc(u, F::p(1), d[0]);
+    d[1] = ptx::madc_hi_cc(u, F::p(1), d[1]);
+#pragma unroll
+    for (int j = 3; j < N; j += 2) {
+      d[j - 1] = ptx::madc_lo_cc(u, F::p(j), d[j - 1]);
+      d[j] = ptx::madc_hi_cc(u, F::p(j), d[j]);
+    }
+    d[N] = ptx::addc(d[N], 0);
+  }
+  // last division by 2^32 and merge: t = d + (c >> 32 bits), t < 2q
+  uint32_t t[N + 1];
+  t[0] = ptx::add_cc(d[0], c[1]);
+#pragma unroll
+  for (int k = 1; k < N; ++k) t[k] = ptx::addc_cc(d[k], c[k + 1]);
+  t[N] = ptx::addc(d[N], 0);
+  uint32_t s[N];
+  s[0] = ptx::sub_cc(t[0], F::p(0));
+#pragma unroll
+  for (int k = 1; k < N; ++k) s[k] = ptx::subc_cc(t[k], F::p(k));
+  const uint32_t top = ptx::subc(t[N], 0);  // 0xffffffff iff t < q
+#pragma unroll
+  for (int k = 0; k < N; ++k) r[k] = top == 0xffffffffu ? t[k] : s[k];
+}
+
+template <class F>
+ECC_DEV void mont_sqr(uint32_t* r, const uint32_t* a) {
+  mont_mul<F>(r, a, a);
+}
+
+// canonical integer -> Montgomery form (a * R^2 * R^-1 = a R)
+template <class F>
+ECC_DEV void to_mont(uint32_t* r, const uint32_t* a) {
+  uint32_t r2[F::N];
+#pragma unroll
+  for (int i = 0; i < F::N; ++i) r2[i] = F::r2(i);
+  mont_mul<F>(r, a, r2);
+}
+
+// Montgomery form -> canonical integer
+template <class F>
+ECC_DEV void from_mont(uint32_t* r, const uint32_t* a) {
+  uint32_t one[F::N];
+#pragma unroll
+  for (int i = 0; i < F::N; ++i) one[i] = i == 0 ? 1u : 0u;
+  mont_mul<F>(r, a, one);
+}
+
+// r = a^(q-2) = a^-1 (Fermat, Section 2.2); a = 0 gives 0.  Fixed 4-bit
+// windows over the exponent, most significant first.  Used by one thread per
+// batch (the "apply" step of the gather-apply-scatter batch inversion).
+template <class F>
+__device__ __noinline__ void fe_inv_fermat(uint32_t* r, const uint32_t* a) {
+  constexpr int N = F::N;
+  uint32_t tab[16][N];
+  fe_set_one<F>(tab[0]);
+  fe_copy<F>(tab[1], a);
+  for (int k = 2; k < 16; ++k) mont_mul<F>(tab[k], tab[k - 1], a);
+  uint32_t acc[N];
+  fe_set_one<F>(acc);
+  for (int w = 8 * N - 1; w >= 0; --w) {
+    const uint32_t digit = (F::pm2(w >> 3) >> (4 * (w & 7))) & 15u;
+    for (int s = 0; s < 4; ++s) mont_sqr<F>(acc, acc);
+    uint32_t t[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) t[i] = tab[digit][i];
+    mont_mul<F>(acc, acc, t);
+  }
+  fe_copy<F>(r, acc);
+}
+
+}  // namespace ecc

@@ -1,0 +1,63 @@
+// Host-side interface between the C ABI (abi.cu) and the kernel translation
+// units.  All pointers are device pointers; all launches are asynchronous on
+// `st` and report launch errors through the returned cudaError_t.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+namespace ecc {
+
+// Stream-ordered device scratch, released at scope exit (cudaFreeAsync on the
+// same stream, so later work on the stream may still be using it safely).
+struct Scratch {
+  void* ptr = nullptr;
+  cudaStream_t st = nullptr;
+  size_t bytes = 0;
+  Scratch() = default;
+  Scratch(const Scratch&) = delete;
+  Scratch& operator=(const Scratch&) = delete;
+  ~Scratch() {
+    if (ptr) cudaFreeAsync(ptr, st);
+  }
+  cudaError_t alloc(size_t b, cudaStream_t s);
+  template <class T>
+  T* as() const {
+    return reinterpret_cast<T*>(ptr);
+  }
+};
+
+int device_sm_count();
+std::string cuda_msg(cudaError_t e);
+
+// field layer: curve 0..3, field 0 = base, 1 = scalar
+cudaError_t launch_fe_mul(int curve, int field, size_t n, const uint32_t* a, const uint32_t* b,
+                          uint32_t* out, cudaStream_t st);
+cudaError_t launch_fe_addsub(int curve, int field, size_t n, const uint32_t* a,
+                             const uint32_t* b, uint32_t* out, int subtract, cudaStream_t st);
+cudaError_t launch_fe_inv(int curve, int field, size_t n, const uint32_t* a, uint32_t* out,
+                          cudaStream_t st);
+cudaError_t launch_fe_inv_batch(int curve, int field, size_t n, const uint32_t* a, uint32_t* out,
+                                cudaStream_t st);
+int field_limbs(int curve, int field);
+
+// EC operators
+cudaError_t launch_point_add(int curve, size_t n, const uint32_t* p, const uint32_t* q,
+                             uint32_t* out, int dbl, cudaStream_t st);
+// Fixed-base table of a curve on the current device (built on first use,
+// synchronously on `st`): 32 x 256 entries, entry j*256+v = v 2^(8j) G, SoA
+// Montgomery (x block then y block).
+cudaError_t gtable(int curve, const uint4** table, cudaStream_t st);
+
+// ECDSA
+cudaError_t launch_verify(int curve, size_t n, const uint8_t* hash, const uint8_t* r,
+                          const uint8_t* s, const uint8_t* pub, uint8_t* ok, cudaStream_t st);
+
+// benchmarks
+cudaError_t launch_bench_imad(size_t threads, int iters, uint32_t* sink, cudaStream_t st);
+cudaError_t launch_bench_modmul(int curve, size_t threads, int iters, uint32_t* sink,
+                                cudaStream_t st);
+
+}  // namespace ecc

@@ -1,0 +1,154 @@
+// Field-layer kernels and launchers: modmul / modadd / modinv unit operations,
+// batch inversion, and the integer multiply-add issue-rate probes.
+#include "internal.h"
+#include "ops.cuh"
+
+namespace ecc {
+
+namespace {
+
+template <class F>
+cudaError_t fe_ops(int op, size_t n, const uint32_t* a, const uint32_t* b, uint32_t* out,
+                   cudaStream_t st) {
+  const int threads = 256;
+  const unsigned blocks = (unsigned)((n + threads - 1) / threads);
+  switch (op) {
+    case 0: k_fe_mul<F><<<blocks, threads, 0, st>>>(a, b, out, n); break;
+    case 1: k_fe_addsub<F><<<blocks, threads, 0, st>>>(a, b, out, n, 0); break;
+    case 2: k_fe_addsub<F><<<blocks, threads, 0, st>>>(a, b, out, n, 1); break;
+    case 3: k_fe_inv_single<F><<<blocks, threads, 0, st>>>(a, out, n); break;
+  }
+  return cudaGetLastError();
+}
+
+template <class F>
+cudaError_t fe_inv_batch(size_t n, const uint32_t* a, uint32_t* out, cudaStream_t st) {
+  constexpr int B = kBlock;
+  Scratch ws;
+  const size_t soa = soa_bytes<F>(n);
+  cudaError_t e = ws.alloc(3 * soa, st);
+  if (e != cudaSuccess) return e;
+  SoA<F> in{ws.as<uint4>(), n}, res{ws.as<uint4>() + soa / 16, n}, M{ws.as<uint4>() + 2 * soa / 16, n};
+  const unsigned cb = (unsigned)((n + 255) / 256);
+  k_fe_in<F><<<cb, 256, 0, st>>>(a, n, F::N, 0, in, 1);
+  // one CTA per (SM x 2) slice, at least a full thread row per CTA
+  size_t ctas = (size_t)device_sm_count() * 2;
+  size_t per = (n + ctas - 1) / ctas;
+  if (per < B) per = B;
+  ctas = (n + per - 1) / per;
+  const size_t smem = sizeof(GasSmem<F::N, B>);
+  e = cudaFuncSetAttribute(k_batch_inverse<F, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+  if (e != cudaSuccess) return e;
+  k_batch_inverse<F, B><<<(unsigned)ctas, B, smem, st>>>(in, res, M, n, per);
+  k_fe_out<F><<<cb, 256, 0, st>>>(res, n, out, F::N, 0, 1);
+  return cudaGetLastError();
+}
+
+template <class F>
+__global__ void k_bench_modmul(int iters, uint32_t* sink) {
+  constexpr int N = F::N;
+  uint32_t x[4][N], y[4][N];
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      x[c][k] = (t * 2654435761u + c * 40503u + k) & (k == N - 1 ? 0x0fffffffu : 0xffffffffu);
+      y[c][k] = F::one(k) ^ (c + k);
+    }
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) mont_mul<F>(x[c], x[c], y[c]);
+  }
+  uint32_t acc = 0;
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int k = 0; k < N; ++k) acc ^= x[c][k];
+  sink[t] = acc;
+}
+
+// 8 independent carry chains of mad.lo.cc / madc.hi pairs per iteration
+__global__ void k_bench_imad(int iters, uint32_t* sink) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t lo[8], hi[8], a[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    lo[c] = t + c;
+    hi[c] = t ^ (c * 977u);
+    a[c] = 0x9E3779B9u + 2u * c + 1u;
+  }
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const uint32_t x = lo[c];
+      lo[c] = ptx::mad_lo_cc(a[c], x, lo[c]);
+      hi[c] = ptx::madc_hi(a[c], x, hi[c]);
+    }
+  }
+  uint32_t acc = 0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) acc ^= lo[c] ^ hi[c];
+  sink[t] = acc;
+}
+
+}  // namespace
+
+int field_limbs(int curve, int field) {
+  if (field == 1) return 8;
+  return curve == 3 ? 12 : 8;
+}
+
+#define ECC_FIELD_DISPATCH(curve, field, CALL)          \
+  switch ((curve) * 2 + (field)) {                      \
+    case 0: { using F = Secp256k1Fp; return CALL; }     \
+    case 1: { using F = Secp256k1Fn; return CALL; }     \
+    case 2: { using F = P256Fp; return CALL; }          \
+    case 3: { using F = P256Fn; return CALL; }          \
+    case 4: { using F = BN254Fp; return CALL; }         \
+    case 5: { using F = BN254Fn; return CALL; }         \
+    case 6: { using F = BLS12_381Fp; return CALL; }     \
+    case 7: { using F = BLS12_381Fn; return CALL; }     \
+  }                                                     \
+  return cudaErrorInvalidValue;
+
+cudaError_t launch_fe_mul(int curve, int field, size_t n, const uint32_t* a, const uint32_t* b,
+                          uint32_t* out, cudaStream_t st) {
+  ECC_FIELD_DISPATCH(curve, field, (fe_ops<F>(0, n, a, b, out, st)))
+}
+
+cudaError_t launch_fe_addsub(int curve, int field, size_t n, const uint32_t* a,
+                             const uint32_t* b, uint32_t* out, int subtract, cudaStream_t st) {
+  ECC_FIELD_DISPATCH(curve, field, (fe_ops<F>(subtract ? 2 : 1, n, a, b, out, st)))
+}
+
+cudaError_t launch_fe_inv(int curve, int field, size_t n, const uint32_t* a, uint32_t* out,
+                          cudaStream_t st) {
+  ECC_FIELD_DISPATCH(curve, field, (fe_ops<F>(3, n, a, nullptr, out, st)))
+}
+
+cudaError_t launch_fe_inv_batch(int curve, int field, size_t n, const uint32_t* a, uint32_t* out,
+                                cudaStream_t st) {
+  ECC_FIELD_DISPATCH(curve, field, (fe_inv_batch<F>(n, a, out, st)))
+}
+
+cudaError_t launch_bench_imad(size_t threads, int iters, uint32_t* sink, cudaStream_t st) {
+  k_bench_imad<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(iters, sink);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bench_modmul(int curve, size_t threads, int iters, uint32_t* sink,
+                                cudaStream_t st) {
+  const unsigned b = (unsigned)((threads + 255) / 256);
+  switch (curve) {
+    case 0: k_bench_modmul<Secp256k1Fp><<<b, 256, 0, st>>>(iters, sink); break;
+    case 1: k_bench_modmul<P256Fp><<<b, 256, 0, st>>>(iters, sink); break;
+    case 2: k_bench_modmul<BN254Fp><<<b, 256, 0, st>>>(iters, sink); break;
+    case 3: k_bench_modmul<BLS12_381Fp><<<b, 256, 0, st>>>(iters, sink); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace ecc

@@ -1,0 +1,71 @@
+// Launcher of the batched ECDSA verification kernel (secp256k1, P-256).
+#include "internal.h"
+#include "verify.cuh"
+
+namespace ecc {
+
+namespace {
+
+constexpr int kVerifyBlock = 256;
+
+template <class C>
+cudaError_t verify(size_t n, const uint8_t* hash, const uint8_t* r, const uint8_t* s,
+                   const uint8_t* pub, uint8_t* ok, cudaStream_t st, int curve) {
+  using Fp = typename C::Fp;
+  using Fn = typename C::Fn;
+  constexpr int B = kVerifyBlock;
+  const uint4* tg = nullptr;
+  cudaError_t e = gtable(curve, &tg, st);
+  if (e != cudaSuccess) return e;
+  // workspace: S, E, Rn (Fn) | TQ x,y (8n each) | AQ, AG | M | D2 | U1B | status
+  const size_t fe = soa_bytes<Fp>(n);
+  const size_t bytes = 3 * fe + 16 * fe + 4 * fe + fe + 65 * n + 32 * n + n + 256;
+  Scratch ws;
+  e = ws.alloc(bytes, st);
+  if (e != cudaSuccess) return e;
+  uint4* v = ws.as<uint4>();
+  const size_t q = fe / 16;  // uint4 per SoA array of n elements
+  VerifyArgs<C> a;
+  a.n = n;
+  a.hash = reinterpret_cast<const uint32_t*>(hash);
+  a.r = reinterpret_cast<const uint32_t*>(r);
+  a.s = reinterpret_cast<const uint32_t*>(s);
+  a.pub = reinterpret_cast<const uint32_t*>(pub);
+  a.ok = ok;
+  a.S = SoA<Fn>{v + 0 * q, n};
+  a.E = SoA<Fn>{v + 1 * q, n};
+  a.Rn = SoA<Fn>{v + 2 * q, n};
+  a.TQ = PtSoA<Fp>{SoA<Fp>{v + 3 * q, 8 * n}, SoA<Fp>{v + 11 * q, 8 * n}};
+  a.AQ = PtSoA<Fp>{SoA<Fp>{v + 19 * q, n}, SoA<Fp>{v + 20 * q, n}};
+  a.AG = PtSoA<Fp>{SoA<Fp>{v + 21 * q, n}, SoA<Fp>{v + 22 * q, n}};
+  a.M = SoA<Fp>{v + 23 * q, n};
+  uint8_t* tail = reinterpret_cast<uint8_t*>(v + 24 * q);
+  a.D2 = reinterpret_cast<int8_t*>(tail);
+  a.U1B = tail + 65 * n;
+  a.status = tail + 97 * n;
+  const size_t te = 32 * 256;
+  a.TG = PtSoA<Fp>{SoA<Fp>{const_cast<uint4*>(tg), te}, SoA<Fp>{const_cast<uint4*>(tg) + soa_bytes<Fp>(te) / 16, te}};
+  size_t ctas = (size_t)device_sm_count() * 2;
+  size_t per = (n + ctas - 1) / ctas;
+  if (per < 32) per = 32;
+  ctas = (n + per - 1) / per;
+  a.per_cta = per;
+  const size_t smem = sizeof(GasSmem<Fp::N, B>);
+  e = cudaFuncSetAttribute(k_verify<C, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_verify<C, B><<<(unsigned)ctas, B, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_verify(int curve, size_t n, const uint8_t* hash, const uint8_t* r,
+                          const uint8_t* s, const uint8_t* pub, uint8_t* ok, cudaStream_t st) {
+  switch (curve) {
+    case 0: return verify<Secp256k1>(n, hash, r, s, pub, ok, st, 0);
+    case 1: return verify<P256>(n, hash, r, s, pub, ok, st, 1);
+  }
+  return cudaErrorNotSupported;
+}
+
+}  // namespace ecc

@@ -1,0 +1,160 @@
+"""Thin Python binding of the C ABI in ``include/gecc.h`` (argument marshalling only).
+
+Every function has the name of the C entry point it calls and takes the same
+arguments; arrays may be torch tensors (CUDA or CPU) or numpy arrays (host), and
+``stream`` may be a ``torch.cuda.Stream``, a raw ``cudaStream_t`` integer, or
+``None`` for torch's current stream on the current device.  All computation
+happens in ``libgecc.so``; there is no Python or CPU fallback: if the library is
+missing, ``load()`` raises.
+"""
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgecc.so")
+
+ECC_SECP256K1, ECC_P256, ECC_BN254, ECC_BLS12_381 = 0, 1, 2, 3
+CURVES = {"secp256k1": 0, "P-256": 1, "BN254": 2, "BLS12-381": 3}
+ECC_FIELD_BASE, ECC_FIELD_SCALAR = 0, 1
+ECC_OK, ECC_EINVAL, ECC_EUNSUPPORTED, ECC_ENOMEM, ECC_ECUDA, ECC_ETIMEOUT = 0, -1, -2, -3, -4, -5
+
+_lock = threading.Lock()
+_lib = None
+
+
+class EccError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+_SIGS = {
+    "ecc_last_error": (ctypes.c_char_p, []),
+    "ecc_version": (ctypes.c_char_p, []),
+    "ecc_limbs": (ctypes.c_int, [ctypes.c_int]),
+    "ecc_fp_mul": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_size_t] + [ctypes.c_void_p] * 4),
+    "ecc_fp_add": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_size_t] + [ctypes.c_void_p] * 4),
+    "ecc_fp_sub": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_size_t] + [ctypes.c_void_p] * 4),
+    "ecc_fp_inv": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_size_t] + [ctypes.c_void_p] * 3),
+    "ecc_fp_inv_batch": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_size_t] + [ctypes.c_void_p] * 3),
+    "ecc_point_add_batch": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t] + [ctypes.c_void_p] * 4),
+    "ecc_point_dbl_batch": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t] + [ctypes.c_void_p] * 3),
+    "ecc_verify_batch": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t] + [ctypes.c_void_p] * 6),
+    "ecc_bench_imad": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "ecc_bench_modmul": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p,
+                                        ctypes.c_void_p]),
+}
+
+
+def load():
+    """Loads libgecc.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"CUDA library {LIB_PATH} is missing: run __graft_entry__.build() first")
+            lib = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                if hasattr(lib, name):
+                    fn = getattr(lib, name)
+                    fn.restype = res
+                    fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def exported_symbols():
+    return sorted(_SIGS)
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):  # torch tensor
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if hasattr(a, "ctypes"):  # numpy array
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if isinstance(a, int):
+        return a
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(rc):
+    if rc != ECC_OK:
+        msg = load().ecc_last_error().decode(errors="replace")
+        raise EccError(rc, msg)
+    return rc
+
+
+def ecc_last_error():
+    return load().ecc_last_error().decode(errors="replace")
+
+
+def ecc_version():
+    return load().ecc_version().decode()
+
+
+def ecc_limbs(curve):
+    rc = load().ecc_limbs(curve)
+    if rc < 0:
+        _check(rc)
+    return rc
+
+
+def ecc_fp_mul(curve, field, n, a, b, out, stream=None):
+    return _check(load().ecc_fp_mul(curve, field, n, _ptr(a), _ptr(b), _ptr(out), _stream(stream)))
+
+
+def ecc_fp_add(curve, field, n, a, b, out, stream=None):
+    return _check(load().ecc_fp_add(curve, field, n, _ptr(a), _ptr(b), _ptr(out), _stream(stream)))
+
+
+def ecc_fp_sub(curve, field, n, a, b, out, stream=None):
+    return _check(load().ecc_fp_sub(curve, field, n, _ptr(a), _ptr(b), _ptr(out), _stream(stream)))
+
+
+def ecc_fp_inv(curve, field, n, a, out, stream=None):
+    return _check(load().ecc_fp_inv(curve, field, n, _ptr(a), _ptr(out), _stream(stream)))
+
+
+def ecc_fp_inv_batch(curve, field, n, a, out, stream=None):
+    return _check(load().ecc_fp_inv_batch(curve, field, n, _ptr(a), _ptr(out), _stream(stream)))
+
+
+def ecc_point_add_batch(curve, n, p, q, out, stream=None):
+    return _check(load().ecc_point_add_batch(curve, n, _ptr(p), _ptr(q), _ptr(out), _stream(stream)))
+
+
+def ecc_point_dbl_batch(curve, n, p, out, stream=None):
+    return _check(load().ecc_point_dbl_batch(curve, n, _ptr(p), _ptr(out), _stream(stream)))
+
+
+def ecc_verify_batch(curve, n, hash, r, s, pubkey, ok_out, stream=None):
+    return _check(load().ecc_verify_batch(curve, n, _ptr(hash), _ptr(r), _ptr(s), _ptr(pubkey),
+                                          _ptr(ok_out), _stream(stream)))
+
+
+def ecc_bench_imad(threads, iters, sink, stream=None):
+    return _check(load().ecc_bench_imad(threads, iters, _ptr(sink), _stream(stream)))
+
+
+def ecc_bench_modmul(curve, threads, iters, sink, stream=None):
+    return _check(load().ecc_bench_modmul(curve, threads, iters, _ptr(sink), _stream(stream)))

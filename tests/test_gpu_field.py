@@ -1,0 +1,90 @@
+"""GPU parity of the field layer (a2 modmul, a3 modadd/modsub, a4 modinv,
+a5 batch inversion) against the oracle's plain definitions, bit-exact."""
+import random
+
+import numpy as np
+import pytest
+
+from oracle import curves, field
+from paper_2501_03245_gb300 import synth
+from tests.helpers import from_cuda, to_cuda
+
+pytestmark = pytest.mark.gpu
+
+CASES = [(cid, f) for cid in range(4) for f in (0, 1)]
+
+
+def _modulus(cid, f):
+    C = curves.BY_ID[cid]
+    return (C.p if f == 0 else C.n), (C.limbs if f == 0 else 8)
+
+
+def _values(q, n, seed):
+    rng = random.Random(seed)
+    edge = [0, 1, 2, q - 1, q - 2, q // 2, (1 << (q.bit_length() - 1)) % q]
+    return (edge + [rng.randrange(q) for _ in range(n)])[:n]
+
+
+@pytest.mark.parametrize("cid,f", CASES)
+def test_fp_mul_add_sub(gpu_lib, cid, f):
+    import torch
+
+    q, m = _modulus(cid, f)
+    n = 2 * 256 + 37  # several blocks and a ragged tail
+    A = _values(q, n, cid * 10 + f)
+    B = list(reversed(_values(q, n, cid * 10 + f + 5)))
+    a, b = to_cuda(synth.ints_to_limbs(A, m)), to_cuda(synth.ints_to_limbs(B, m))
+    out = torch.zeros_like(a)
+    for op, ref in ((gpu_lib.ecc_fp_mul, field.mul), (gpu_lib.ecc_fp_add, field.add),
+                    (gpu_lib.ecc_fp_sub, field.sub)):
+        op(cid, f, n, a, b, out)
+        torch.cuda.synchronize()
+        got = synth.limbs_to_ints(from_cuda(out))
+        assert got == [ref(q, x, y) for x, y in zip(A, B)], op.__name__
+
+
+@pytest.mark.parametrize("cid,f", CASES)
+def test_fp_inverse_single_and_batch(gpu_lib, cid, f):
+    import torch
+
+    q, m = _modulus(cid, f)
+    for n in (1, 255, 3 * 512 + 7):
+        X = _values(q, n, n + cid)
+        if n > 10:
+            X[3] = 0
+            X[n // 2] = 0
+        x = to_cuda(synth.ints_to_limbs(X, m))
+        out = torch.zeros_like(x)
+        want = field.batch_inverse(q, X)
+        gpu_lib.ecc_fp_inv_batch(cid, f, n, x, out)
+        torch.cuda.synchronize()
+        assert synth.limbs_to_ints(from_cuda(out)) == want
+        if n <= 255:
+            gpu_lib.ecc_fp_inv(cid, f, n, x, out)
+            torch.cuda.synchronize()
+            assert synth.limbs_to_ints(from_cuda(out)) == [field.inv(q, v) for v in X]
+
+
+def test_host_memory_staging(gpu_lib):
+    """The same call with host (numpy) buffers stages through the device."""
+    q, m = _modulus(1, 0)
+    A, B = _values(q, 300, 1), _values(q, 300, 2)
+    a, b = synth.ints_to_limbs(A, m), synth.ints_to_limbs(B, m)
+    out = np.zeros_like(a)
+    gpu_lib.ecc_fp_mul(1, 0, 300, a, b, out)
+    assert synth.limbs_to_ints(out) == [x * y % q for x, y in zip(A, B)]
+
+
+def test_argument_errors(gpu_lib):
+    import torch
+
+    a = torch.zeros((4, 8), dtype=torch.int32, device="cuda")
+    with pytest.raises(gpu_lib.EccError) as e:
+        gpu_lib.ecc_fp_mul(9, 0, 4, a, a, a)
+    assert e.value.code == gpu_lib.ECC_EINVAL
+    with pytest.raises(gpu_lib.EccError):
+        gpu_lib.ecc_fp_mul(0, 0, 4, None, a, a)
+    gpu_lib.ecc_fp_mul(0, 0, 0, None, None, None)  # n = 0 is a no-op
+    with pytest.raises(gpu_lib.EccError) as e:
+        gpu_lib.ecc_verify_batch(2, 4, a, a, a, a, a)
+    assert e.value.code == gpu_lib.ECC_EUNSUPPORTED
