@@ -121,6 +121,24 @@ int ecc_point_dbl_batch(ecc_curve_t curve, size_t n, const uint32_t* p, uint32_t
 int ecc_verify_batch(ecc_curve_t curve, size_t n, const uint8_t* hash, const uint8_t* r,
                      const uint8_t* s, const uint8_t* pubkey, uint8_t* ok_out, void* stream);
 
+/* ---------------------------------------------------------------- FPMUL
+ * out[i] = k[i] * G (fixed-point multiplication, Section 2.1.1 and Table 5:
+ * the generator's table v 2^(8j) G removes every PDBL; 32 batched affine
+ * additions per scalar).  k: n x 8 limbs (any 256-bit integer); out: n affine
+ * points ((0, 0) when k[i] * G = O). */
+int ecc_fixed_base_mul(ecc_curve_t curve, size_t n, const uint32_t* k, uint32_t* out,
+                       void* stream);
+
+/* Batched ECDSA signing (Section 5.2: one modinv plus one FPMUL; SEC 1 section
+ * 4.1.3 with the nonce supplied by the caller): r = x(k G) mod n,
+ * s = k^-1 (e + r d) mod n, and the public key d G.
+ * curve: ECC_SECP256K1 or ECC_P256.  d, e, k: n x 32 bytes big-endian;
+ * r_out, s_out: n x 32 bytes; pub_out: n x 64 bytes (x || y).  An item with d
+ * or k outside [1, n-1], or whose nonce gives r = 0 or s = 0, gets r = s = 0. */
+int ecc_sign_batch(ecc_curve_t curve, size_t n, const uint8_t* d, const uint8_t* e,
+                   const uint8_t* k, uint8_t* r_out, uint8_t* s_out, uint8_t* pub_out,
+                   void* stream);
+
 /* ---------------------------------------------------------------- benchmarks
  * Integer multiply-add issue-rate probe (the microbenchmark method of
  * Section 4.1, Table 2): each of `threads` threads runs `iters` iterations of

@@ -1,0 +1,69 @@
+"""Algorithmic work counts used for the roofline (no GPU code, no arithmetic of
+the method itself -- only operation counts).
+
+Basis (fixed, whatever reduction a kernel uses):
+  * one modmul or modsqr of an m-limb field costs 2 m^2 + m 32-bit wide
+    multiply-adds (m^2 for the product, m^2 + m for the Montgomery reduction;
+    Section 4.1: 136 for m = 8);
+  * affine PADD = 1 modinv + 3 modmul and PDBL = 1 modinv + 4 modmul (Table 1);
+    inside a batch Montgomery's trick replaces the modinv by 3 modmul
+    (Section 2.2.1), so a batched PADD costs 6 and a batched PDBL 7 modmul
+    (Section 3.1: "6N modmul" for N PADDs).  The per-batch modinv and the
+    gather tree are overhead, not counted.
+"""
+
+# Table 1 (affine column) and Section 2.2.1
+PADD_FORMULA_MODMUL = 3
+PDBL_FORMULA_MODMUL = 4
+TRICK_MODMUL_PER_ELEMENT = 3
+BATCH_PADD_MODMUL = PADD_FORMULA_MODMUL + TRICK_MODMUL_PER_ELEMENT   # 6
+BATCH_PDBL_MODMUL = PDBL_FORMULA_MODMUL + TRICK_MODMUL_PER_ELEMENT   # 7
+
+# ECDSA verification schedule of the verification kernel
+Q_WINDOWS = 65          # signed radix-16 digits of u2 (64 + carry digit)
+Q_DOUBLINGS = 64 * 4    # 4 doublings between consecutive windows
+G_COMB_ADDS = 32        # fixed-base comb, 8-bit windows
+TABLE_DBL, TABLE_ADD = 4, 3   # {2Q, 4Q, 6Q, 8Q} doublings, {3Q, 5Q, 7Q} additions
+FINAL_ADDS = 1          # R = u1 G + u2 Q
+SCALAR_MODMUL = 3 + 2 + 2   # batched s^-1 (trick), u1 and u2, two conversions out
+PREP_MODMUL = 5 + 4         # five conversions into Montgomery form, on-curve check
+
+
+def imad_per_modmul(limbs):
+    """Wide multiply-adds of one Montgomery multiplication (Section 4.1)."""
+    return 2 * limbs * limbs + limbs
+
+
+def verify_modmul():
+    """Algorithmic modmul per ECDSA verification (256-bit curves)."""
+    dbl = Q_DOUBLINGS + TABLE_DBL
+    add = Q_WINDOWS + G_COMB_ADDS + TABLE_ADD + FINAL_ADDS
+    return dbl * BATCH_PDBL_MODMUL + add * BATCH_PADD_MODMUL + SCALAR_MODMUL + PREP_MODMUL
+
+
+def verify_imad():
+    return verify_modmul() * imad_per_modmul(8)
+
+
+def fpmul_modmul():
+    """Algorithmic modmul per fixed-base multiplication k G (32 comb additions)."""
+    return G_COMB_ADDS * BATCH_PADD_MODMUL
+
+
+def break_even_batch(inv_over_mul=100):
+    """Smallest batch N for which 1 modinv + 6N modmul < 11N modmul
+    (affine batch vs Jacobian PADD, Section 3.1) with modinv = inv_over_mul modmul."""
+    n = 1
+    while inv_over_mul + 6 * n >= 11 * n:
+        n += 1
+    return n
+
+
+def msm_modmul(n_points, windows, c, buckets_touched=None):
+    """Algorithmic modmul of one Pippenger MSM with batch-affine bucket
+    accumulation: one batched PADD per (point, window) digit, the bucket
+    reduction (two additions per bucket) and the window combination
+    (c doublings + 1 addition per window)."""
+    buckets = windows * (1 << (c - 1)) if buckets_touched is None else buckets_touched
+    return (n_points * windows * BATCH_PADD_MODMUL + 2 * buckets * BATCH_PADD_MODMUL
+            + windows * (c * BATCH_PDBL_MODMUL + BATCH_PADD_MODMUL))

@@ -264,6 +264,44 @@ int ecc_verify_batch(ecc_curve_t curve, size_t n, const uint8_t* hash, const uin
   });
 }
 
+int ecc_fixed_base_mul(ecc_curve_t curve, size_t n, const uint32_t* k, uint32_t* out,
+                       void* stream) {
+  const char* name = "ecc_fixed_base_mul";
+  if (!valid_curve(curve)) return fail(ECC_EINVAL, "%s: unknown curve %d", name, (int)curve);
+  if (n == 0) return ok();
+  if (!k || !out) return fail(ECC_EINVAL, "%s: NULL pointer", name);
+  if (!aligned4(k) || !aligned4(out)) return fail(ECC_EINVAL, "%s: pointers must be 4-byte aligned", name);
+  if (n > (size_t)1 << 27) return fail(ECC_EINVAL, "%s: n > 2^27", name);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Arg K(k, 32 * n), O(out, n * 8 * field_limbs(curve, 0));
+  return with_args(name, st, {&K}, {&O}, [&]() {
+    return launch_fixed_base_mul(curve, n, static_cast<const uint32_t*>(K.dev),
+                                 static_cast<uint32_t*>(O.dev), st);
+  });
+}
+
+int ecc_sign_batch(ecc_curve_t curve, size_t n, const uint8_t* d, const uint8_t* e,
+                   const uint8_t* k, uint8_t* r_out, uint8_t* s_out, uint8_t* pub_out,
+                   void* stream) {
+  const char* name = "ecc_sign_batch";
+  if (!valid_curve(curve)) return fail(ECC_EINVAL, "%s: unknown curve %d", name, (int)curve);
+  if (curve != ECC_SECP256K1 && curve != ECC_P256)
+    return fail(ECC_EUNSUPPORTED, "%s: ECDSA is offered on secp256k1 and P-256", name);
+  if (n == 0) return ok();
+  if (!d || !e || !k || !r_out || !s_out || !pub_out) return fail(ECC_EINVAL, "%s: NULL pointer", name);
+  if (!aligned4(d) || !aligned4(e) || !aligned4(k) || !aligned4(r_out) || !aligned4(s_out) ||
+      !aligned4(pub_out))
+    return fail(ECC_EINVAL, "%s: pointers must be 4-byte aligned", name);
+  if (n > (size_t)1 << 26) return fail(ECC_EINVAL, "%s: n > 2^26", name);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Arg D(d, 32 * n), E(e, 32 * n), K(k, 32 * n), R(r_out, 32 * n), S(s_out, 32 * n), P(pub_out, 64 * n);
+  return with_args(name, st, {&D, &E, &K}, {&R, &S, &P}, [&]() {
+    return launch_sign(curve, n, static_cast<const uint8_t*>(D.dev), static_cast<const uint8_t*>(E.dev),
+                       static_cast<const uint8_t*>(K.dev), static_cast<uint8_t*>(R.dev),
+                       static_cast<uint8_t*>(S.dev), static_cast<uint8_t*>(P.dev), st);
+  });
+}
+
 int ecc_bench_imad(size_t threads, int iters, uint32_t* sink, void* stream) {
   if (threads == 0 || iters < 0 || !sink) return fail(ECC_EINVAL, "ecc_bench_imad: bad argument");
   cudaError_t e = launch_bench_imad(threads, iters, sink, static_cast<cudaStream_t>(stream));

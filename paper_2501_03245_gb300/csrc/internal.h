@@ -51,7 +51,13 @@ cudaError_t launch_point_add(int curve, size_t n, const uint32_t* p, const uint3
 // Montgomery (x block then y block).
 cudaError_t gtable(int curve, const uint4** table, cudaStream_t st);
 
+// FPMUL k_i G (scalars n x 8 LE limbs; out n x 2N LE limbs)
+cudaError_t launch_fixed_base_mul(int curve, size_t n, const uint32_t* k, uint32_t* out,
+                                  cudaStream_t st);
+
 // ECDSA
+cudaError_t launch_sign(int curve, size_t n, const uint8_t* d, const uint8_t* e, const uint8_t* k,
+                        uint8_t* r, uint8_t* s, uint8_t* pub, cudaStream_t st);
 cudaError_t launch_verify(int curve, size_t n, const uint8_t* hash, const uint8_t* r,
                           const uint8_t* s, const uint8_t* pub, uint8_t* ok, cudaStream_t st);
 

@@ -41,6 +41,8 @@ _SIGS = {
     "ecc_point_add_batch": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t] + [ctypes.c_void_p] * 4),
     "ecc_point_dbl_batch": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t] + [ctypes.c_void_p] * 3),
     "ecc_verify_batch": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t] + [ctypes.c_void_p] * 6),
+    "ecc_fixed_base_mul": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t] + [ctypes.c_void_p] * 3),
+    "ecc_sign_batch": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t] + [ctypes.c_void_p] * 7),
     "ecc_bench_imad": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "ecc_bench_modmul": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p,
                                         ctypes.c_void_p]),
@@ -150,6 +152,15 @@ def ecc_point_dbl_batch(curve, n, p, out, stream=None):
 def ecc_verify_batch(curve, n, hash, r, s, pubkey, ok_out, stream=None):
     return _check(load().ecc_verify_batch(curve, n, _ptr(hash), _ptr(r), _ptr(s), _ptr(pubkey),
                                           _ptr(ok_out), _stream(stream)))
+
+
+def ecc_fixed_base_mul(curve, n, k, out, stream=None):
+    return _check(load().ecc_fixed_base_mul(curve, n, _ptr(k), _ptr(out), _stream(stream)))
+
+
+def ecc_sign_batch(curve, n, d, e, k, r_out, s_out, pub_out, stream=None):
+    return _check(load().ecc_sign_batch(curve, n, _ptr(d), _ptr(e), _ptr(k), _ptr(r_out),
+                                        _ptr(s_out), _ptr(pub_out), _stream(stream)))
 
 
 def ecc_bench_imad(threads, iters, sink, stream=None):

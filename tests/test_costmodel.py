@@ -1,0 +1,35 @@
+"""The roofline's work counts against the counts the paper prints
+(tests/golden/paper_counts.json, each entry cited there)."""
+import json
+import os
+
+from paper_2501_03245_gb300 import costmodel
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_counts.json")))
+
+
+def test_table1_and_trick():
+    assert costmodel.PADD_FORMULA_MODMUL == GOLDEN["affine_padd"]["modmul"]
+    assert costmodel.PDBL_FORMULA_MODMUL == GOLDEN["affine_pdbl"]["modmul"]
+    assert costmodel.TRICK_MODMUL_PER_ELEMENT == GOLDEN["montgomery_trick"]["modmul_per_element"]
+    assert costmodel.BATCH_PADD_MODMUL == GOLDEN["batch_padd_modmul_per_op"]["value"]
+
+
+def test_imad_count_per_modmul():
+    g = GOLDEN["imad_modmul_256"]
+    assert costmodel.imad_per_modmul(8) == g["total"] == g["product"] + g["reduction"]
+    assert costmodel.imad_per_modmul(12) == 300
+
+
+def test_break_even():
+    ratio = GOLDEN["modinv_over_modadd"]["value"] // GOLDEN["modmul_over_modadd"]["value"]
+    jac = GOLDEN["jacobian_padd"]["modmul"]
+    assert ratio == 100 and jac == 11
+    assert costmodel.break_even_batch(ratio) == GOLDEN["break_even_batch_exclusive"]["value"] + 1
+
+
+def test_verify_count_structure():
+    m = costmodel.verify_modmul()
+    assert m == 260 * 7 + 101 * 6 + 7 + 9
+    assert costmodel.verify_imad() == m * 136
+    assert costmodel.fpmul_modmul() == 32 * 6
