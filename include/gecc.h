@@ -139,6 +139,42 @@ int ecc_sign_batch(ecc_curve_t curve, size_t n, const uint8_t* d, const uint8_t*
                    const uint8_t* k, uint8_t* r_out, uint8_t* s_out, uint8_t* pub_out,
                    void* stream);
 
+/* ---------------------------------------------------------------- MSM
+ * Multi-scalar multiplication out = sum_i k_i P_i (Pippenger's bucket method
+ * with batched affine bucket accumulation; the paper's batch inversion and
+ * PADD, Sections 3.2-3.3).  Curves: ECC_BN254 and ECC_BLS12_381 (others give
+ * ECC_EUNSUPPORTED).  Points: n affine points (canonical, (0, 0) = O,
+ * assumed in the prime-order subgroup); scalars: n x 8 limbs, any 256-bit value
+ * (reduced mod the group order r).  out: one affine point (2 * ecc_limbs()
+ * limbs), (0, 0) when the sum is O.  The window width follows the size class
+ * (ecc_msm_window). */
+int ecc_msm(ecc_curve_t curve, size_t n, const uint32_t* points, const uint32_t* scalars,
+            uint32_t* out, void* stream);
+
+/* `num` independent MSMs in one launch sequence (one digit / sort /
+ * accumulation pass over all of them, per-instance window widths).
+ * offsets: HOST array of num + 1 row indices; instance i uses rows
+ * [offsets[i], offsets[i+1]) of points and scalars; empty instances give O.
+ * out: num points.  No host synchronisation inside: with device buffers the
+ * call can be captured in a CUDA graph and replayed. */
+int ecc_msm_ragged(ecc_curve_t curve, size_t num, const uint64_t* offsets, const uint32_t* points,
+                   const uint32_t* scalars, uint32_t* out, void* stream);
+
+/* Resident bases: convert n points once into the library's device layout
+ * (owned by the handle until ecc_bases_destroy), then run MSMs of many scalar
+ * vectors against them.  ecc_msm_bases: scalars = num_vectors x n x 8 limbs,
+ * out = num_vectors points; all vectors run through the same launches. */
+int ecc_bases_create(ecc_curve_t curve, size_t n, const uint32_t* points, void** handle,
+                     void* stream);
+int ecc_msm_bases(void* handle, size_t num_vectors, const uint32_t* scalars, uint32_t* out,
+                  void* stream);
+int ecc_bases_destroy(void* handle);
+
+/* Window width used for an n-point MSM, and the autotuner's override for the
+ * size class floor(log2 n) (c = 0 restores the cost-model default). */
+int ecc_msm_window(ecc_curve_t curve, size_t n);
+int ecc_msm_set_window(ecc_curve_t curve, int log2_n, int c);
+
 /* ---------------------------------------------------------------- benchmarks
  * Integer multiply-add issue-rate probe (the microbenchmark method of
  * Section 4.1, Table 2): each of `threads` threads runs `iters` iterations of

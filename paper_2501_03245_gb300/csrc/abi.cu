@@ -1,7 +1,9 @@
 // C ABI (include/gecc.h): argument checks, host-memory staging, error strings.
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
+#include <string>
 #include <vector>
 
 #include "../../include/gecc.h"
@@ -300,6 +302,114 @@ int ecc_sign_batch(ecc_curve_t curve, size_t n, const uint8_t* d, const uint8_t*
                        static_cast<const uint8_t*>(K.dev), static_cast<uint8_t*>(R.dev),
                        static_cast<uint8_t*>(S.dev), static_cast<uint8_t*>(P.dev), st);
   });
+}
+
+int ecc_msm_ragged(ecc_curve_t curve, size_t num, const uint64_t* offsets, const uint32_t* points,
+                   const uint32_t* scalars, uint32_t* out, void* stream) {
+  const char* name = "ecc_msm_ragged";
+  if (!valid_curve(curve)) return fail(ECC_EINVAL, "%s: unknown curve %d", name, (int)curve);
+  if (curve != ECC_BN254 && curve != ECC_BLS12_381)
+    return fail(ECC_EUNSUPPORTED, "%s: MSM is offered on BN254 and BLS12-381", name);
+  if (num == 0) return ok();
+  if (!offsets || !out) return fail(ECC_EINVAL, "%s: NULL pointer", name);
+  if (num > (1u << 20)) return fail(ECC_EINVAL, "%s: num > 2^20", name);
+  if (!host_memory(offsets)) return fail(ECC_EINVAL, "%s: offsets must be host memory", name);
+  for (size_t i = 0; i < num; ++i)
+    if (offsets[i + 1] < offsets[i]) return fail(ECC_EINVAL, "%s: offsets must not decrease", name);
+  const uint64_t rows = offsets[num] - offsets[0];
+  if (rows > (1ull << 28)) return fail(ECC_EINVAL, "%s: more than 2^28 points", name);
+  if (rows && (!points || !scalars)) return fail(ECC_EINVAL, "%s: NULL pointer", name);
+  if ((points && !aligned4(points)) || (scalars && !aligned4(scalars)) || !aligned4(out))
+    return fail(ECC_EINVAL, "%s: pointers must be 4-byte aligned", name);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int L = field_limbs(curve, 0);
+  const uint32_t* pb = points ? points + offsets[0] * 2 * L : points;
+  const uint32_t* sb = scalars ? scalars + offsets[0] * 8 : scalars;
+  std::vector<uint64_t> rel(num + 1);
+  for (size_t i = 0; i <= num; ++i) rel[i] = offsets[i] - offsets[0];
+  Arg P(pb ? pb : out, std::max<uint64_t>(rows, 1) * 2 * L * 4);
+  Arg S(sb ? sb : out, std::max<uint64_t>(rows, 1) * 32);
+  Arg O(out, num * 2 * L * 4);
+  std::vector<Arg*> ins;
+  if (rows) {
+    ins.push_back(&P);
+    ins.push_back(&S);
+  }
+  return with_args(name, st, ins, {&O}, [&]() {
+    return launch_msm(curve, (uint32_t)num, rel.data(), static_cast<const uint32_t*>(P.dev),
+                      static_cast<const uint32_t*>(S.dev), static_cast<uint32_t*>(O.dev), st);
+  });
+}
+
+int ecc_msm(ecc_curve_t curve, size_t n, const uint32_t* points, const uint32_t* scalars,
+            uint32_t* out, void* stream) {
+  uint64_t off[2] = {0, n};
+  int rc = ecc_msm_ragged(curve, 1, off, points, scalars, out, stream);
+  if (rc != ECC_OK) {
+    std::string m = g_err;
+    size_t k = m.find("ecc_msm_ragged");
+    if (k != std::string::npos) m.replace(k, 14, "ecc_msm");
+    fail(rc, "%s", m.c_str());
+  }
+  return rc;
+}
+
+int ecc_bases_create(ecc_curve_t curve, size_t n, const uint32_t* points, void** handle,
+                     void* stream) {
+  const char* name = "ecc_bases_create";
+  if (!valid_curve(curve)) return fail(ECC_EINVAL, "%s: unknown curve %d", name, (int)curve);
+  if (curve != ECC_BN254 && curve != ECC_BLS12_381)
+    return fail(ECC_EUNSUPPORTED, "%s: MSM is offered on BN254 and BLS12-381", name);
+  if (!handle || (n && !points)) return fail(ECC_EINVAL, "%s: NULL pointer", name);
+  if (points && !aligned4(points)) return fail(ECC_EINVAL, "%s: pointers must be 4-byte aligned", name);
+  if (n > (1ull << 28)) return fail(ECC_EINVAL, "%s: n > 2^28", name);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int L = field_limbs(curve, 0);
+  Arg P(points ? points : (const uint32_t*)handle, std::max<size_t>(n, 1) * 2 * L * 4);
+  std::vector<Arg*> ins;
+  if (n) ins.push_back(&P);
+  return with_args(name, st, ins, {}, [&]() {
+    return bases_create(curve, n, static_cast<const uint32_t*>(P.dev), handle, st);
+  });
+}
+
+int ecc_msm_bases(void* handle, size_t num_vectors, const uint32_t* scalars, uint32_t* out,
+                  void* stream) {
+  const char* name = "ecc_msm_bases";
+  if (!handle) return fail(ECC_EINVAL, "%s: NULL handle", name);
+  if (num_vectors == 0) return ok();
+  if (!scalars || !out) return fail(ECC_EINVAL, "%s: NULL pointer", name);
+  if (!aligned4(scalars) || !aligned4(out)) return fail(ECC_EINVAL, "%s: pointers must be 4-byte aligned", name);
+  if (num_vectors > 4096) return fail(ECC_EINVAL, "%s: num_vectors > 4096", name);
+  const int curve = bases_curve(handle);
+  const uint64_t n = bases_count(handle);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int L = field_limbs(curve, 0);
+  Arg S(scalars, std::max<uint64_t>(n, 1) * num_vectors * 32), O(out, num_vectors * 2 * L * 4);
+  return with_args(name, st, {&S}, {&O}, [&]() {
+    return launch_msm_bases(handle, (uint32_t)num_vectors, static_cast<const uint32_t*>(S.dev),
+                            static_cast<uint32_t*>(O.dev), st);
+  });
+}
+
+int ecc_bases_destroy(void* handle) {
+  if (!handle) return fail(ECC_EINVAL, "ecc_bases_destroy: NULL handle");
+  cudaError_t e = bases_destroy(handle);
+  if (e != cudaSuccess) return cuda_fail(e, "ecc_bases_destroy");
+  return ok();
+}
+
+int ecc_msm_window(ecc_curve_t curve, size_t n) {
+  if (!valid_curve(curve)) return fail(ECC_EINVAL, "ecc_msm_window: unknown curve %d", (int)curve);
+  return msm_window(curve, n);
+}
+
+int ecc_msm_set_window(ecc_curve_t curve, int log2_n, int c) {
+  if (!valid_curve(curve)) return fail(ECC_EINVAL, "ecc_msm_set_window: unknown curve %d", (int)curve);
+  if (log2_n < 0 || log2_n > 40 || c < 0 || c > 20 || c == 1)
+    return fail(ECC_EINVAL, "ecc_msm_set_window: need 0 <= log2_n <= 40 and c = 0 or 2..20");
+  msm_set_window(curve, log2_n, c);
+  return ok();
 }
 
 int ecc_bench_imad(size_t threads, int iters, uint32_t* sink, void* stream) {

@@ -61,6 +61,20 @@ cudaError_t launch_sign(int curve, size_t n, const uint8_t* d, const uint8_t* e,
 cudaError_t launch_verify(int curve, size_t n, const uint8_t* hash, const uint8_t* r,
                           const uint8_t* s, const uint8_t* pub, uint8_t* ok, cudaStream_t st);
 
+// MSM: `num` instances, instance i = points / scalars rows
+// [offsets[i] - offsets[0], offsets[i+1] - offsets[0]) (host offsets); out: num x 2N limbs
+int msm_window(int curve, uint64_t n);
+void msm_set_window(int curve, int log2n, int c);
+cudaError_t launch_msm(int curve, uint32_t num, const uint64_t* offsets, const uint32_t* points,
+                       const uint32_t* scalars, uint32_t* out, cudaStream_t st);
+cudaError_t bases_create(int curve, uint64_t n, const uint32_t* points, void** handle,
+                         cudaStream_t st);
+cudaError_t bases_destroy(void* handle);
+int bases_curve(void* handle);
+uint64_t bases_count(void* handle);
+cudaError_t launch_msm_bases(void* handle, uint32_t num_vectors, const uint32_t* scalars,
+                             uint32_t* out, cudaStream_t st);
+
 // benchmarks
 cudaError_t launch_bench_imad(size_t threads, int iters, uint32_t* sink, cudaStream_t st);
 cudaError_t launch_bench_modmul(int curve, size_t threads, int iters, uint32_t* sink,

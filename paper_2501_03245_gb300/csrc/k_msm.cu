@@ -1,0 +1,118 @@
+// MSM entry points shared by all curves: window-width table (cost model and
+// autotuner overrides), resident bases, and dispatch to the per-curve
+// translation units (k_msm_bn254.cu, k_msm_bls12_381.cu).
+#include <algorithm>
+#include <map>
+#include <mutex>
+
+#include "msm_host.cuh"
+
+namespace ecc {
+
+cudaError_t msm_points_bn254(uint32_t num, const uint64_t* offsets, const uint32_t* points,
+                             const uint32_t* scalars, uint32_t* out, cudaStream_t st);
+cudaError_t msm_points_bls12_381(uint32_t num, const uint64_t* offsets, const uint32_t* points,
+                                 const uint32_t* scalars, uint32_t* out, cudaStream_t st);
+cudaError_t msm_bases_bn254(void* bases, uint32_t num_vectors, const uint32_t* scalars,
+                            uint32_t* out, cudaStream_t st);
+cudaError_t msm_bases_bls12_381(void* bases, uint32_t num_vectors, const uint32_t* scalars,
+                                uint32_t* out, cudaStream_t st);
+cudaError_t points_to_mont(int curve, const uint32_t* in, uint64_t n, uint32_t* out,
+                           cudaStream_t st);
+
+namespace {
+
+std::mutex g_win_mu;
+std::map<std::pair<int, int>, int> g_window_table;  // (curve, floor(log2 n)) -> c
+
+// Cost model: one batched addition (6 modmul) per (point, window) digit plus the
+// Jacobian bucket reduction (about three additions of ~15 modmul per bucket).
+int model_window(int curve, uint64_t n) {
+  int best = 4;
+  double best_cost = 1e300;
+  for (int c = 4; c <= 20; ++c) {
+    const double W = msm_detail::windows_for(curve, c);
+    const double cost = (double)n * W * 6.0 + W * (double)(1u << (c - 1)) * 45.0;
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = c;
+    }
+  }
+  return best;
+}
+
+int ilog2(uint64_t n) {
+  int l = 0;
+  while ((n >> 1) > 0) {
+    n >>= 1;
+    ++l;
+  }
+  return l;
+}
+
+}  // namespace
+
+int msm_window(int curve, uint64_t n) {
+  if (n < 2) n = 2;
+  {
+    std::lock_guard<std::mutex> lock(g_win_mu);
+    auto it = g_window_table.find({curve, ilog2(n)});
+    if (it != g_window_table.end()) return it->second;
+  }
+  return model_window(curve, n);
+}
+
+void msm_set_window(int curve, int log2n, int c) {
+  std::lock_guard<std::mutex> lock(g_win_mu);
+  if (c <= 0) {
+    g_window_table.erase({curve, log2n});
+  } else {
+    g_window_table[{curve, log2n}] = c;
+  }
+}
+
+cudaError_t launch_msm(int curve, uint32_t num, const uint64_t* offsets, const uint32_t* points,
+                       const uint32_t* scalars, uint32_t* out, cudaStream_t st) {
+  switch (curve) {
+    case 2: return msm_points_bn254(num, offsets, points, scalars, out, st);
+    case 3: return msm_points_bls12_381(num, offsets, points, scalars, out, st);
+  }
+  return cudaErrorNotSupported;
+}
+
+cudaError_t bases_create(int curve, uint64_t n, const uint32_t* points, void** handle,
+                         cudaStream_t st) {
+  if (curve != 2 && curve != 3) return cudaErrorNotSupported;
+  const int N = curve == 3 ? 12 : 8;
+  uint32_t* m = nullptr;
+  cudaError_t e = cudaMalloc(&m, std::max<uint64_t>(n, 1) * 2 * N * 4);
+  if (e != cudaSuccess) return e;
+  if (n) e = points_to_mont(curve, points, n, m, st);
+  if (e != cudaSuccess) {
+    cudaFree(m);
+    return e;
+  }
+  *handle = new msm_detail::Bases{curve, n, m};
+  return cudaSuccess;
+}
+
+int bases_curve(void* handle) { return static_cast<msm_detail::Bases*>(handle)->curve; }
+uint64_t bases_count(void* handle) { return static_cast<msm_detail::Bases*>(handle)->n; }
+
+cudaError_t bases_destroy(void* handle) {
+  auto* b = static_cast<msm_detail::Bases*>(handle);
+  cudaError_t e = cudaFree(b->mont);
+  delete b;
+  return e;
+}
+
+cudaError_t launch_msm_bases(void* handle, uint32_t num_vectors, const uint32_t* scalars,
+                             uint32_t* out, cudaStream_t st) {
+  switch (bases_curve(handle)) {
+    case 2: return msm_bases_bn254(handle, num_vectors, scalars, out, st);
+    case 3: return msm_bases_bls12_381(handle, num_vectors, scalars, out, st);
+  }
+  return cudaErrorNotSupported;
+}
+
+}  // namespace ecc

@@ -1,0 +1,24 @@
+// MSM instantiation for BLS12_381 (one translation unit per curve so the library
+// builds in parallel).
+#include "msm_host.cuh"
+
+namespace ecc {
+
+cudaError_t msm_points_bls12_381(uint32_t num, const uint64_t* offsets, const uint32_t* points,
+                                 const uint32_t* scalars, uint32_t* out, cudaStream_t st) {
+  return msm_detail::msm_points<BLS12_381>(3, num, offsets, points, scalars, out, st);
+}
+
+cudaError_t msm_bases_bls12_381(void* bases, uint32_t num_vectors, const uint32_t* scalars,
+                                uint32_t* out, cudaStream_t st) {
+  return msm_detail::msm_bases_t<BLS12_381>(static_cast<msm_detail::Bases*>(bases), num_vectors, scalars,
+                                     out, st);
+}
+
+cudaError_t points_to_mont_bls12_381(const uint32_t* in, uint64_t n, uint32_t* out,
+                                     cudaStream_t st) {
+  k_points_to_mont<BLS12_381><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(in, n, out);
+  return cudaGetLastError();
+}
+
+}  // namespace ecc

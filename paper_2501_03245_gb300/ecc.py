@@ -43,6 +43,13 @@ _SIGS = {
     "ecc_verify_batch": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t] + [ctypes.c_void_p] * 6),
     "ecc_fixed_base_mul": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t] + [ctypes.c_void_p] * 3),
     "ecc_sign_batch": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t] + [ctypes.c_void_p] * 7),
+    "ecc_msm": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t] + [ctypes.c_void_p] * 4),
+    "ecc_msm_ragged": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t] + [ctypes.c_void_p] * 5),
+    "ecc_bases_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t] + [ctypes.c_void_p] * 3),
+    "ecc_msm_bases": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t] + [ctypes.c_void_p] * 3),
+    "ecc_bases_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "ecc_msm_window": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t]),
+    "ecc_msm_set_window": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "ecc_bench_imad": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "ecc_bench_modmul": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p,
                                         ctypes.c_void_p]),
@@ -161,6 +168,45 @@ def ecc_fixed_base_mul(curve, n, k, out, stream=None):
 def ecc_sign_batch(curve, n, d, e, k, r_out, s_out, pub_out, stream=None):
     return _check(load().ecc_sign_batch(curve, n, _ptr(d), _ptr(e), _ptr(k), _ptr(r_out),
                                         _ptr(s_out), _ptr(pub_out), _stream(stream)))
+
+
+def ecc_msm(curve, n, points, scalars, out, stream=None):
+    return _check(load().ecc_msm(curve, n, _ptr(points), _ptr(scalars), _ptr(out), _stream(stream)))
+
+
+def ecc_msm_ragged(curve, num, offsets, points, scalars, out, stream=None):
+    """offsets: host array (numpy uint64 or list) of num + 1 row indices."""
+    import numpy as np
+
+    offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.uint64))
+    return _check(load().ecc_msm_ragged(curve, num, offs.ctypes.data, _ptr(points), _ptr(scalars),
+                                        _ptr(out), _stream(stream)))
+
+
+def ecc_bases_create(curve, n, points, stream=None):
+    """Returns the opaque handle (an int)."""
+    h = ctypes.c_void_p()
+    _check(load().ecc_bases_create(curve, n, _ptr(points), ctypes.addressof(h), _stream(stream)))
+    return h.value
+
+
+def ecc_msm_bases(handle, num_vectors, scalars, out, stream=None):
+    return _check(load().ecc_msm_bases(handle, num_vectors, _ptr(scalars), _ptr(out), _stream(stream)))
+
+
+def ecc_bases_destroy(handle):
+    return _check(load().ecc_bases_destroy(handle))
+
+
+def ecc_msm_window(curve, n):
+    rc = load().ecc_msm_window(curve, n)
+    if rc < 0:
+        _check(rc)
+    return rc
+
+
+def ecc_msm_set_window(curve, log2_n, c):
+    return _check(load().ecc_msm_set_window(curve, log2_n, c))
 
 
 def ecc_bench_imad(threads, iters, sink, stream=None):
