@@ -11,6 +11,7 @@ struct Secp256k1Fp {
   static constexpr int N = 8;
   static constexpr int BITS = 256;
   static constexpr uint32_t QINV = 0xd2253531u;
+  static constexpr uint64_t QINV62 = 0x27c7f6e22ddacacfull;  // q^-1 mod 2^62
   ECC_DEV static constexpr uint32_t p(int i) {
     switch (i) { case 0: return 0xfffffc2fu; case 1: return 0xfffffffeu; case 2: return 0xffffffffu; case 3: return 0xffffffffu; case 4: return 0xffffffffu; case 5: return 0xffffffffu; case 6: return 0xffffffffu; case 7: return 0xffffffffu; default: return 0u; }
   }
@@ -23,12 +24,16 @@ struct Secp256k1Fp {
   ECC_DEV static constexpr uint32_t pm2(int i) {
     switch (i) { case 0: return 0xfffffc2du; case 1: return 0xfffffffeu; case 2: return 0xffffffffu; case 3: return 0xffffffffu; case 4: return 0xffffffffu; case 5: return 0xffffffffu; case 6: return 0xffffffffu; case 7: return 0xffffffffu; default: return 0u; }
   }
+  ECC_DEV static constexpr uint32_t r3(int i) {
+    switch (i) { case 0: return 0x3795f671u; case 1: return 0x002bb1e3u; case 2: return 0x00000b73u; case 3: return 0x00000001u; case 4: return 0x00000000u; case 5: return 0x00000000u; case 6: return 0x00000000u; case 7: return 0x00000000u; default: return 0u; }
+  }
 };
 
 struct Secp256k1Fn {
   static constexpr int N = 8;
   static constexpr int BITS = 256;
   static constexpr uint32_t QINV = 0x5588b13fu;
+  static constexpr uint64_t QINV62 = 0x34f20099aa774ec1ull;  // q^-1 mod 2^62
   ECC_DEV static constexpr uint32_t p(int i) {
     switch (i) { case 0: return 0xd0364141u; case 1: return 0xbfd25e8cu; case 2: return 0xaf48a03bu; case 3: return 0xbaaedce6u; case 4: return 0xfffffffeu; case 5: return 0xffffffffu; case 6: return 0xffffffffu; case 7: return 0xffffffffu; default: return 0u; }
   }
@@ -40,6 +45,9 @@ struct Secp256k1Fn {
   }
   ECC_DEV static constexpr uint32_t pm2(int i) {
     switch (i) { case 0: return 0xd036413fu; case 1: return 0xbfd25e8cu; case 2: return 0xaf48a03bu; case 3: return 0xbaaedce6u; case 4: return 0xfffffffeu; case 5: return 0xffffffffu; case 6: return 0xffffffffu; case 7: return 0xffffffffu; default: return 0u; }
+  }
+  ECC_DEV static constexpr uint32_t r3(int i) {
+    switch (i) { case 0: return 0xe9ff41edu; case 1: return 0x7bc0cfe0u; case 2: return 0x44d4322cu; case 3: return 0x00176484u; case 4: return 0xf1d0b2dau; case 5: return 0xb1b31347u; case 6: return 0x18ef116du; case 7: return 0x555d800cu; default: return 0u; }
   }
 };
 
@@ -69,6 +77,7 @@ struct P256Fp {
   static constexpr int N = 8;
   static constexpr int BITS = 256;
   static constexpr uint32_t QINV = 0x00000001u;
+  static constexpr uint64_t QINV62 = 0x3fffffffffffffffull;  // q^-1 mod 2^62
   ECC_DEV static constexpr uint32_t p(int i) {
     switch (i) { case 0: return 0xffffffffu; case 1: return 0xffffffffu; case 2: return 0xffffffffu; case 3: return 0x00000000u; case 4: return 0x00000000u; case 5: return 0x00000000u; case 6: return 0x00000001u; case 7: return 0xffffffffu; default: return 0u; }
   }
@@ -81,12 +90,16 @@ struct P256Fp {
   ECC_DEV static constexpr uint32_t pm2(int i) {
     switch (i) { case 0: return 0xfffffffdu; case 1: return 0xffffffffu; case 2: return 0xffffffffu; case 3: return 0x00000000u; case 4: return 0x00000000u; case 5: return 0x00000000u; case 6: return 0x00000001u; case 7: return 0xffffffffu; default: return 0u; }
   }
+  ECC_DEV static constexpr uint32_t r3(int i) {
+    switch (i) { case 0: return 0x0000000au; case 1: return 0xfffffffdu; case 2: return 0xfffffff7u; case 3: return 0xffffffedu; case 4: return 0xfffffffcu; case 5: return 0x00000005u; case 6: return 0x00000001u; case 7: return 0x00000018u; default: return 0u; }
+  }
 };
 
 struct P256Fn {
   static constexpr int N = 8;
   static constexpr int BITS = 256;
   static constexpr uint32_t QINV = 0xee00bc4fu;
+  static constexpr uint64_t QINV62 = 0x332e375511ff43b1ull;  // q^-1 mod 2^62
   ECC_DEV static constexpr uint32_t p(int i) {
     switch (i) { case 0: return 0xfc632551u; case 1: return 0xf3b9cac2u; case 2: return 0xa7179e84u; case 3: return 0xbce6faadu; case 4: return 0xffffffffu; case 5: return 0xffffffffu; case 6: return 0x00000000u; case 7: return 0xffffffffu; default: return 0u; }
   }
@@ -98,6 +111,9 @@ struct P256Fn {
   }
   ECC_DEV static constexpr uint32_t pm2(int i) {
     switch (i) { case 0: return 0xfc63254fu; case 1: return 0xf3b9cac2u; case 2: return 0xa7179e84u; case 3: return 0xbce6faadu; case 4: return 0xffffffffu; case 5: return 0xffffffffu; case 6: return 0x00000000u; case 7: return 0xffffffffu; default: return 0u; }
+  }
+  ECC_DEV static constexpr uint32_t r3(int i) {
+    switch (i) { case 0: return 0x0b65a624u; case 1: return 0xac8ebec9u; case 2: return 0x0c0555c9u; case 3: return 0x111f28aeu; case 4: return 0x6ba5e93fu; case 5: return 0x2543b924u; case 6: return 0x6407be65u; case 7: return 0x503a54e7u; default: return 0u; }
   }
 };
 
@@ -127,6 +143,7 @@ struct BN254Fp {
   static constexpr int N = 8;
   static constexpr int BITS = 254;
   static constexpr uint32_t QINV = 0xe4866389u;
+  static constexpr uint64_t QINV62 = 0x382df87d1b799c77ull;  // q^-1 mod 2^62
   ECC_DEV static constexpr uint32_t p(int i) {
     switch (i) { case 0: return 0xd87cfd47u; case 1: return 0x3c208c16u; case 2: return 0x6871ca8du; case 3: return 0x97816a91u; case 4: return 0x8181585du; case 5: return 0xb85045b6u; case 6: return 0xe131a029u; case 7: return 0x30644e72u; default: return 0u; }
   }
@@ -139,12 +156,16 @@ struct BN254Fp {
   ECC_DEV static constexpr uint32_t pm2(int i) {
     switch (i) { case 0: return 0xd87cfd45u; case 1: return 0x3c208c16u; case 2: return 0x6871ca8du; case 3: return 0x97816a91u; case 4: return 0x8181585du; case 5: return 0xb85045b6u; case 6: return 0xe131a029u; case 7: return 0x30644e72u; default: return 0u; }
   }
+  ECC_DEV static constexpr uint32_t r3(int i) {
+    switch (i) { case 0: return 0xda1530dfu; case 1: return 0xb1cd6dafu; case 2: return 0xa7283db6u; case 3: return 0x62f210e6u; case 4: return 0x0ada0afbu; case 5: return 0xef7f0b0cu; case 6: return 0x2d592544u; case 7: return 0x20fd6e90u; default: return 0u; }
+  }
 };
 
 struct BN254Fn {
   static constexpr int N = 8;
   static constexpr int BITS = 254;
   static constexpr uint32_t QINV = 0xefffffffu;
+  static constexpr uint64_t QINV62 = 0x3d1e0a6c10000001ull;  // q^-1 mod 2^62
   ECC_DEV static constexpr uint32_t p(int i) {
     switch (i) { case 0: return 0xf0000001u; case 1: return 0x43e1f593u; case 2: return 0x79b97091u; case 3: return 0x2833e848u; case 4: return 0x8181585du; case 5: return 0xb85045b6u; case 6: return 0xe131a029u; case 7: return 0x30644e72u; default: return 0u; }
   }
@@ -156,6 +177,9 @@ struct BN254Fn {
   }
   ECC_DEV static constexpr uint32_t pm2(int i) {
     switch (i) { case 0: return 0xefffffffu; case 1: return 0x43e1f593u; case 2: return 0x79b97091u; case 3: return 0x2833e848u; case 4: return 0x8181585du; case 5: return 0xb85045b6u; case 6: return 0xe131a029u; case 7: return 0x30644e72u; default: return 0u; }
+  }
+  ECC_DEV static constexpr uint32_t r3(int i) {
+    switch (i) { case 0: return 0xb4bf0040u; case 1: return 0x5e94d8e1u; case 2: return 0x1cfbb6b8u; case 3: return 0x2a489cbeu; case 4: return 0xa19fcfedu; case 5: return 0x893cc664u; case 6: return 0x7fcc657cu; case 7: return 0x0cf8594bu; default: return 0u; }
   }
 };
 
@@ -185,6 +209,7 @@ struct BLS12_381Fp {
   static constexpr int N = 12;
   static constexpr int BITS = 381;
   static constexpr uint32_t QINV = 0xfffcfffdu;
+  static constexpr uint64_t QINV62 = 0x360c000300030003ull;  // q^-1 mod 2^62
   ECC_DEV static constexpr uint32_t p(int i) {
     switch (i) { case 0: return 0xffffaaabu; case 1: return 0xb9feffffu; case 2: return 0xb153ffffu; case 3: return 0x1eabfffeu; case 4: return 0xf6b0f624u; case 5: return 0x6730d2a0u; case 6: return 0xf38512bfu; case 7: return 0x64774b84u; case 8: return 0x434bacd7u; case 9: return 0x4b1ba7b6u; case 10: return 0x397fe69au; case 11: return 0x1a0111eau; default: return 0u; }
   }
@@ -197,12 +222,16 @@ struct BLS12_381Fp {
   ECC_DEV static constexpr uint32_t pm2(int i) {
     switch (i) { case 0: return 0xffffaaa9u; case 1: return 0xb9feffffu; case 2: return 0xb153ffffu; case 3: return 0x1eabfffeu; case 4: return 0xf6b0f624u; case 5: return 0x6730d2a0u; case 6: return 0xf38512bfu; case 7: return 0x64774b84u; case 8: return 0x434bacd7u; case 9: return 0x4b1ba7b6u; case 10: return 0x397fe69au; case 11: return 0x1a0111eau; default: return 0u; }
   }
+  ECC_DEV static constexpr uint32_t r3(int i) {
+    switch (i) { case 0: return 0xd94ca1e0u; case 1: return 0xed48ac6bu; case 2: return 0x03a7adf8u; case 3: return 0x315f831eu; case 4: return 0x615e29ddu; case 5: return 0x9a53352au; case 6: return 0x921e1761u; case 7: return 0x34c04e5eu; case 8: return 0x65724728u; case 9: return 0x2512d435u; case 10: return 0x91755d4du; case 11: return 0x0aa63460u; default: return 0u; }
+  }
 };
 
 struct BLS12_381Fn {
   static constexpr int N = 8;
   static constexpr int BITS = 255;
   static constexpr uint32_t QINV = 0xffffffffu;
+  static constexpr uint64_t QINV62 = 0x0000000100000001ull;  // q^-1 mod 2^62
   ECC_DEV static constexpr uint32_t p(int i) {
     switch (i) { case 0: return 0x00000001u; case 1: return 0xffffffffu; case 2: return 0xfffe5bfeu; case 3: return 0x53bda402u; case 4: return 0x09a1d805u; case 5: return 0x3339d808u; case 6: return 0x299d7d48u; case 7: return 0x73eda753u; default: return 0u; }
   }
@@ -214,6 +243,9 @@ struct BLS12_381Fn {
   }
   ECC_DEV static constexpr uint32_t pm2(int i) {
     switch (i) { case 0: return 0xffffffffu; case 1: return 0xfffffffeu; case 2: return 0xfffe5bfeu; case 3: return 0x53bda402u; case 4: return 0x09a1d805u; case 5: return 0x3339d808u; case 6: return 0x299d7d48u; case 7: return 0x73eda753u; default: return 0u; }
+  }
+  ECC_DEV static constexpr uint32_t r3(int i) {
+    switch (i) { case 0: return 0x439b73afu; case 1: return 0xc62c1807u; case 2: return 0x8cf06990u; case 3: return 0x1b3e0d18u; case 4: return 0xc7b5f418u; case 5: return 0x73d13c71u; case 6: return 0xc8db33e9u; case 7: return 0x6e2a5bb9u; default: return 0u; }
   }
 };
 

@@ -197,7 +197,8 @@ ECC_DEV void dbl_finish(uint32_t* xr, uint32_t* yr, bool live, const uint32_t* i
 // Per-CTA gather-apply-scatter inversion (Section 3.2).  Every thread brings
 // the product of its own chain; every thread gets back the inverse of its own
 // product.  Gather: a butterfly product tree inside each warp (shuffles), then
-// the warp totals in shared memory; apply: one thread inverts the CTA total;
+// the warp totals in shared memory; apply: one thread inverts the CTA total
+// (divstep inversion, the shortest serial chain available to one thread);
 // scatter: the tree walked back down (each level peels the partner subtree).
 template <int N, int BLOCK>
 struct GasSmem {
@@ -246,7 +247,7 @@ __device__ void cta_invert(uint32_t* out, const uint32_t* in, GasSmem<F::N, BLOC
     fe_copy<F>(pre[0], sm.warp_tot[0]);
     for (int w = 1; w < NW; ++w) mont_mul<F>(pre[w], pre[w - 1], sm.warp_tot[w]);
     uint32_t acc[N];
-    fe_inv_fermat<F>(acc, pre[NW - 1]);
+    fe_inv_mont<F>(acc, pre[NW - 1]);
     for (int w = NW - 1; w >= 1; --w) {
       mont_mul<F>(t, acc, pre[w - 1]);
 #pragma unroll

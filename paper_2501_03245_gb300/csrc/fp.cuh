@@ -22,6 +22,7 @@
 #pragma once
 #include <cstdint>
 
+#include "inv.cuh"
 #include "ptx.cuh"
 
 namespace ecc {
@@ -258,6 +259,24 @@ __device__ __noinline__ void fe_inv_fermat(uint32_t* r, const uint32_t* a) {
     mont_mul<F>(acc, acc, t);
   }
   fe_copy<F>(r, acc);
+}
+
+// r = a^-1 in Montgomery form (a = x R -> r = x^-1 R), a = 0 gives 0, by the
+// divstep inversion of inv.cuh: (x R)^-1 is computed on the integer, then one
+// Montgomery product with R^3 mod q restores the form.  Out of line: it runs on
+// one thread per batch.
+template <class F>
+__device__ __noinline__ void fe_inv_mont(uint32_t* r, const uint32_t* a) {
+  constexpr int N = F::N;
+  constexpr int L = (32 * N + 2 + 61) / 62;
+  uint32_t q[N], x[N], r3[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    q[i] = F::p(i);
+    r3[i] = F::r3(i);
+  }
+  inv_divsteps<L>(x, a, q, N, F::QINV62);
+  mont_mul<F>(r, x, r3);
 }
 
 }  // namespace ecc

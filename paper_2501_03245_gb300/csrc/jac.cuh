@@ -196,7 +196,7 @@ __device__ __noinline__ void jac_to_affine(uint32_t* x, uint32_t* y, const Jac<t
     return;
   }
   uint32_t zi[N], zi2[N];
-  fe_inv_fermat<F>(zi, P.Z);
+  fe_inv_mont<F>(zi, P.Z);
   mont_sqr<F>(zi2, zi);
   mont_mul<F>(x, P.X, zi2);
   mont_mul<F>(zi2, zi2, zi);
