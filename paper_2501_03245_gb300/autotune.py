@@ -1,0 +1,79 @@
+"""Measured window-width autotuner for MSM size classes.
+
+For every size class floor(log2 n) the tuner times ``ecc_msm`` on seeded
+synthetic inputs for the cost model's window width and its neighbours, keeps the
+fastest, installs it with ``ecc_msm_set_window`` and can persist the table as
+JSON (keyed by GPU name and curve) so a later process reloads it instead of
+measuring again.  Inputs are made on the device by the library itself
+(``ecc_fixed_base_mul`` for the bases), so tuning needs no CPU arithmetic.
+"""
+import json
+import os
+
+from . import ecc, synth
+
+
+def _curve_order(curve):
+    # group orders of the MSM curves (BN254 r, BLS12-381 r)
+    return {
+        ecc.ECC_BN254: 0x30644E72E131A029B85045B68181585D2833E84879B9709143E1F593F0000001,
+        ecc.ECC_BLS12_381: 0x73EDA753299D7D483339D80809A1D80553BDA402FFFE5BFEFFFFFFFF00000001,
+    }[curve]
+
+
+def make_bases(curve, n, seed, torch):
+    """n bases a_i G (a_i seeded, uniform in [1, r-1]) as a device tensor."""
+    a = synth.uniform_limbs(seed, synth.S_BASE_MULT, n, _curve_order(curve), lo=1)
+    limbs = ecc.ecc_limbs(curve)
+    out = torch.empty((n, 2 * limbs), dtype=torch.int32, device="cuda")
+    ecc.ecc_fixed_base_mul(curve, n, torch.from_numpy(a.view("int32")).cuda(), out)
+    return out
+
+
+def time_msm(curve, bases, scalars, n, torch, reps=3):
+    out = torch.empty((1, 2 * ecc.ecc_limbs(curve)), dtype=torch.int32, device="cuda")
+    ecc.ecc_msm(curve, n, bases, scalars, out)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        ecc.ecc_msm(curve, n, bases, scalars, out)
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps / 1e3
+
+
+def tune(curve, log2_sizes, torch, spread=2, seed=0x6ECC7777, cache=None):
+    """Returns {log2_n: c} and installs it in the library."""
+    key = None
+    table = {}
+    if cache and os.path.exists(cache):
+        key = f"{torch.cuda.get_device_name()}|{curve}"
+        saved = json.load(open(cache)).get(key, {})
+        table = {int(k): int(v) for k, v in saved.items()}
+    missing = [l for l in log2_sizes if l not in table]
+    if missing:
+        n_max = 1 << max(missing)
+        bases = make_bases(curve, n_max, seed, torch)
+        ks = synth.uniform_limbs(seed, synth.S_SCALAR, n_max, _curve_order(curve))
+        scalars = torch.from_numpy(ks.view("int32")).cuda()
+        for l in missing:
+            n = 1 << l
+            ecc.ecc_msm_set_window(curve, l, 0)
+            c0 = ecc.ecc_msm_window(curve, n)
+            best = None
+            for c in range(max(2, c0 - spread), min(20, c0 + spread) + 1):
+                ecc.ecc_msm_set_window(curve, l, c)
+                t = time_msm(curve, bases, scalars, n, torch)
+                if best is None or t < best[0]:
+                    best = (t, c)
+            table[l] = best[1]
+    for l, c in table.items():
+        ecc.ecc_msm_set_window(curve, l, c)
+    if cache:
+        key = key or f"{torch.cuda.get_device_name()}|{curve}"
+        data = json.load(open(cache)) if os.path.exists(cache) else {}
+        data[key] = {str(k): v for k, v in sorted(table.items())}
+        with open(cache, "w") as f:
+            json.dump(data, f, indent=1)
+    return table
