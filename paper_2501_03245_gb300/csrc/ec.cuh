@@ -37,7 +37,7 @@ struct SoA {
       vec[g * stride + i] = make_uint4(r[4 * g + 0], r[4 * g + 1], r[4 * g + 2], r[4 * g + 3]);
     }
   }
-  ECC_DEV SoA at(size_t offset) const { return SoA{vec + offset, stride}; }
+  __host__ __device__ __forceinline__ SoA at(size_t offset) const { return SoA{vec + offset, stride}; }
 };
 
 template <class F>
