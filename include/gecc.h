@@ -187,6 +187,13 @@ int ecc_bench_imad(size_t threads, int iters, uint32_t* sink, void* stream);
  * 4 independent mont_mul chains of the curve's base field.  sink as above. */
 int ecc_bench_modmul(ecc_curve_t curve, size_t threads, int iters, uint32_t* sink, void* stream);
 
+/* Inversion latency probe: each thread runs a chain of `iters` dependent
+ * inversions in the curve's base field, method 0 = Fermat (Section 2.2),
+ * 1 = divsteps (the GAS apply step).  With threads = 1 the kernel time / iters
+ * is the latency of one inversion on one thread. */
+int ecc_bench_inv(ecc_curve_t curve, int method, size_t threads, int iters, uint32_t* sink,
+                  void* stream);
+
 #ifdef __cplusplus
 }
 #endif

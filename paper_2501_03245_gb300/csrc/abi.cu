@@ -427,4 +427,14 @@ int ecc_bench_modmul(ecc_curve_t curve, size_t threads, int iters, uint32_t* sin
   return ok();
 }
 
+int ecc_bench_inv(ecc_curve_t curve, int method, size_t threads, int iters, uint32_t* sink,
+                  void* stream) {
+  if (!valid_curve(curve)) return fail(ECC_EINVAL, "ecc_bench_inv: unknown curve");
+  if ((method != 0 && method != 1) || threads == 0 || iters < 0 || !sink)
+    return fail(ECC_EINVAL, "ecc_bench_inv: bad argument");
+  cudaError_t e = launch_bench_inv(curve, method, threads, iters, sink, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "ecc_bench_inv");
+  return ok();
+}
+
 }  // extern "C"

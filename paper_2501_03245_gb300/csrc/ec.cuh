@@ -200,6 +200,13 @@ ECC_DEV void dbl_finish(uint32_t* xr, uint32_t* yr, bool live, const uint32_t* i
 // the warp totals in shared memory; apply: one thread inverts the CTA total
 // (divstep inversion, the shortest serial chain available to one thread);
 // scatter: the tree walked back down (each level peels the partner subtree).
+// One batch-inversion group per CTA of kGasThreads threads; kGasCtasPerSm such
+// CTAs are resident per SM (128 registers per thread), so while one CTA waits
+// for its group's inversion the other three keep the SM's multiply-add pipe busy.
+constexpr int kGasThreads = 128;
+constexpr int kGasCtasPerSm = 4;
+constexpr int kGasResidentThreads = kGasThreads * kGasCtasPerSm;
+
 template <int N, int BLOCK>
 struct GasSmem {
   static constexpr int NW = BLOCK / 32;
@@ -242,23 +249,35 @@ __device__ void cta_invert(uint32_t* out, const uint32_t* in, GasSmem<F::N, BLOC
     for (int i = 0; i < N; ++i) sm.warp_tot[warp][i] = v[i];
   }
   __syncthreads();
-  if (tid == 0) {
-    uint32_t pre[NW][N];
-    fe_copy<F>(pre[0], sm.warp_tot[0]);
-    for (int w = 1; w < NW; ++w) mont_mul<F>(pre[w], pre[w - 1], sm.warp_tot[w]);
-    uint32_t acc[N];
-    fe_inv_mont<F>(acc, pre[NW - 1]);
-    for (int w = NW - 1; w >= 1; --w) {
-      mont_mul<F>(t, acc, pre[w - 1]);
+  if (warp == 0) {
+    // the same butterfly over the warp totals (lanes >= NW carry 1), so the
+    // serial part is log2(NW) products up, one inversion, log2(NW) down
+    constexpr int LW = NW <= 1 ? 0 : (NW <= 2 ? 1 : (NW <= 4 ? 2 : (NW <= 8 ? 3 : (NW <= 16 ? 4 : 5))));
+    uint32_t w[N], keep[LW > 0 ? LW : 1][N];
+    if (lane < NW) {
 #pragma unroll
-      for (int i = 0; i < N; ++i) sm.warp_inv[w][i] = t[i];
-      uint32_t tw[N];
-#pragma unroll
-      for (int i = 0; i < N; ++i) tw[i] = sm.warp_tot[w][i];
-      mont_mul<F>(acc, acc, tw);
+      for (int i = 0; i < N; ++i) w[i] = sm.warp_tot[lane][i];
+    } else {
+      fe_set_one<F>(w);
     }
 #pragma unroll
-    for (int i = 0; i < N; ++i) sm.warp_inv[0][i] = acc[i];
+    for (int l = 0; l < LW; ++l) {
+      fe_copy<F>(keep[l], w);
+      fe_shfl_xor<F>(t, w, 1 << l);
+      mont_mul<F>(w, w, t);
+    }
+    if (lane == 0) fe_inv_mont<F>(w, w);
+#pragma unroll
+    for (int i = 0; i < N; ++i) w[i] = __shfl_sync(0xffffffffu, w[i], 0);
+#pragma unroll
+    for (int l = LW - 1; l >= 0; --l) {
+      fe_shfl_xor<F>(t, keep[l], 1 << l);
+      mont_mul<F>(w, w, t);
+    }
+    if (lane < NW) {
+#pragma unroll
+      for (int i = 0; i < N; ++i) sm.warp_inv[lane][i] = w[i];
+    }
   }
   __syncthreads();
 #pragma unroll

@@ -158,7 +158,7 @@ __device__ void fixed_prep(const FixedArgs<C>& a, size_t begin, size_t end) {
 }
 
 template <class C, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 2) k_fixed_base(FixedArgs<C> a) {
+__global__ void __launch_bounds__(BLOCK, kGasResidentThreads / BLOCK) k_fixed_base(FixedArgs<C> a) {
   using Fp = typename C::Fp;
   using Fn = typename C::Fn;
   constexpr int N = Fp::N;

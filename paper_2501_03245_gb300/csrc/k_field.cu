@@ -32,7 +32,7 @@ cudaError_t fe_inv_batch(size_t n, const uint32_t* a, uint32_t* out, cudaStream_
   const unsigned cb = (unsigned)((n + 255) / 256);
   k_fe_in<F><<<cb, 256, 0, st>>>(a, n, F::N, 0, in, 1);
   // one CTA per (SM x 2) slice, at least a full thread row per CTA
-  size_t ctas = (size_t)device_sm_count() * 2;
+  size_t ctas = (size_t)device_sm_count() * kGasCtasPerSm;
   size_t per = (n + ctas - 1) / ctas;
   if (per < B) per = B;
   ctas = (n + per - 1) / per;
@@ -66,6 +66,29 @@ __global__ void k_bench_modmul(int iters, uint32_t* sink) {
   for (int c = 0; c < 4; ++c)
 #pragma unroll
     for (int k = 0; k < N; ++k) acc ^= x[c][k];
+  sink[t] = acc;
+}
+
+// a chain of `iters` dependent inversions per thread: method 0 Fermat, 1 divsteps
+template <class F>
+__global__ void k_bench_inv(int method, int iters, uint32_t* sink) {
+  constexpr int N = F::N;
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t x[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) x[k] = F::one(k) ^ (t * 2654435761u + k);
+  x[N - 1] &= 0x0fffffffu;
+  for (int it = 0; it < iters; ++it) {
+    if (method == 0) {
+      fe_inv_fermat<F>(x, x);
+    } else {
+      fe_inv_mont<F>(x, x);
+    }
+    x[0] ^= 1u;  // never a fixed point
+  }
+  uint32_t acc = 0;
+#pragma unroll
+  for (int k = 0; k < N; ++k) acc ^= x[k];
   sink[t] = acc;
 }
 
@@ -135,6 +158,20 @@ cudaError_t launch_fe_inv_batch(int curve, int field, size_t n, const uint32_t* 
 
 cudaError_t launch_bench_imad(size_t threads, int iters, uint32_t* sink, cudaStream_t st) {
   k_bench_imad<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(iters, sink);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bench_inv(int curve, int method, size_t threads, int iters, uint32_t* sink,
+                             cudaStream_t st) {
+  const unsigned t = (unsigned)(threads < 128 ? threads : 128);
+  const unsigned b = (unsigned)((threads + t - 1) / t);
+  switch (curve) {
+    case 0: k_bench_inv<Secp256k1Fp><<<b, t, 0, st>>>(method, iters, sink); break;
+    case 1: k_bench_inv<P256Fp><<<b, t, 0, st>>>(method, iters, sink); break;
+    case 2: k_bench_inv<BN254Fp><<<b, t, 0, st>>>(method, iters, sink); break;
+    case 3: k_bench_inv<BLS12_381Fp><<<b, t, 0, st>>>(method, iters, sink); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

@@ -6,7 +6,7 @@ namespace ecc {
 
 namespace {
 
-constexpr int kFixedBlock = 256;
+constexpr int kFixedBlock = kGasThreads;
 
 template <class C>
 cudaError_t fixed_base(int curve, int mode, size_t n, const uint32_t* k, const uint32_t* d,
@@ -49,7 +49,7 @@ cudaError_t fixed_base(int curve, int mode, size_t n, const uint32_t* k, const u
   const size_t te = 32 * 256;
   a.TG = PtSoA<Fp>{SoA<Fp>{const_cast<uint4*>(tg), te},
                    SoA<Fp>{const_cast<uint4*>(tg) + soa_bytes<Fp>(te) / 16, te}};
-  size_t ctas = (size_t)device_sm_count() * 2;
+  size_t ctas = (size_t)device_sm_count() * kGasCtasPerSm;
   size_t per = (n + ctas - 1) / ctas;
   if (per < 32) per = 32;
   ctas = (n + per - 1) / per;

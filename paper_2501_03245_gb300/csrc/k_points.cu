@@ -38,7 +38,7 @@ cudaError_t run_ops(PtSoA<typename C::Fp> pool, const PointOp* ops, size_t n_ops
   constexpr int B = kBlock;
   using F = typename C::Fp;
   if (n_ops == 0) return cudaSuccess;
-  size_t ctas = (size_t)device_sm_count() * 2;
+  size_t ctas = (size_t)device_sm_count() * kGasCtasPerSm;
   size_t per = (n_ops + ctas - 1) / ctas;
   if (per < B) per = B;
   ctas = (n_ops + per - 1) / per;

@@ -6,7 +6,7 @@ namespace ecc {
 
 namespace {
 
-constexpr int kVerifyBlock = 256;
+constexpr int kVerifyBlock = kGasThreads;
 
 template <class C>
 cudaError_t verify(size_t n, const uint8_t* hash, const uint8_t* r, const uint8_t* s,
@@ -45,7 +45,7 @@ cudaError_t verify(size_t n, const uint8_t* hash, const uint8_t* r, const uint8_
   a.status = tail + 97 * n;
   const size_t te = 32 * 256;
   a.TG = PtSoA<Fp>{SoA<Fp>{const_cast<uint4*>(tg), te}, SoA<Fp>{const_cast<uint4*>(tg) + soa_bytes<Fp>(te) / 16, te}};
-  size_t ctas = (size_t)device_sm_count() * 2;
+  size_t ctas = (size_t)device_sm_count() * kGasCtasPerSm;
   size_t per = (n + ctas - 1) / ctas;
   if (per < 32) per = 32;
   ctas = (n + per - 1) / per;

@@ -236,7 +236,7 @@ struct AccRound {
 };
 
 template <class C, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 2) k_msm_accumulate(AccArgs<C> a) {
+__global__ void __launch_bounds__(BLOCK, kGasResidentThreads / BLOCK) k_msm_accumulate(AccArgs<C> a) {
   using F = typename C::Fp;
   constexpr int N = F::N;
   auto& sm = gas_smem<N, BLOCK>();

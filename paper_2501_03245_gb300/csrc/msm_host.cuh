@@ -16,7 +16,7 @@ namespace ecc {
 
 namespace msm_detail {
 
-constexpr int kAccBlock = 256;
+constexpr int kAccBlock = kGasThreads;
 constexpr uint32_t kReduceChunk = 32;
 
 inline int scalar_bits(int curve) {
@@ -93,7 +93,7 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
   a.S = PtSoA<F>{SoA<F>{sbuf, NC}, SoA<F>{sbuf + sz_S / 16, NC}};
   a.M = SoA<F>{sbuf + 2 * sz_S / 16, NC};
   a.partial = PtSoA<F>{SoA<F>{pbuf, n_part}, SoA<F>{pbuf + sz_P / 16, n_part}};
-  uint64_t ctas = (uint64_t)device_sm_count() * 2;
+  uint64_t ctas = (uint64_t)device_sm_count() * kGasCtasPerSm;
   uint64_t per = (NC + ctas - 1) / ctas;
   if (per < 32) per = 32;
   ctas = (NC + per - 1) / per;

@@ -10,7 +10,7 @@
 
 namespace ecc {
 
-constexpr int kBlock = 256;
+constexpr int kBlock = kGasThreads;
 
 // ---------------------------------------------------------------- conversion
 
@@ -125,7 +125,7 @@ struct InvRound {
 // a5: out = in^-1 elementwise (Montgomery form, 0 -> 0); each CTA inverts the
 // contiguous slice [blockIdx.x * per_cta, ...) with one modular inversion.
 template <class F, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_batch_inverse(SoA<F> in, SoA<F> out, SoA<F> M,
+__global__ void __launch_bounds__(BLOCK, kGasResidentThreads / BLOCK) k_batch_inverse(SoA<F> in, SoA<F> out, SoA<F> M,
                                                          size_t n, size_t per_cta) {
   auto& sm = gas_smem<F::N, BLOCK>();
   const size_t begin = blockIdx.x * per_cta;
@@ -166,7 +166,7 @@ struct OpRound {
 // a6/a7: one batched round of independent point operations.  No op of a launch
 // may read a slot that another op of the same launch writes.
 template <class C, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_point_ops(PtSoA<typename C::Fp> pool,
+__global__ void __launch_bounds__(BLOCK, kGasResidentThreads / BLOCK) k_point_ops(PtSoA<typename C::Fp> pool,
                                                      const PointOp* ops, size_t n_ops,
                                                      SoA<typename C::Fp> M, size_t per_cta) {
   auto& sm = gas_smem<C::Fp::N, BLOCK>();

@@ -336,7 +336,7 @@ struct FinalRound {
 };
 
 template <class C, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 2) k_verify(VerifyArgs<C> a) {
+__global__ void __launch_bounds__(BLOCK, kGasResidentThreads / BLOCK) k_verify(VerifyArgs<C> a) {
   using Fp = typename C::Fp;
   using Fn = typename C::Fn;
   static_assert(Fp::N == 8 && Fn::N == 8, "256-bit curves");

@@ -51,6 +51,8 @@ _SIGS = {
     "ecc_msm_window": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t]),
     "ecc_msm_set_window": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "ecc_bench_imad": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "ecc_bench_inv": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_size_t, ctypes.c_int,
+                                     ctypes.c_void_p, ctypes.c_void_p]),
     "ecc_bench_modmul": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p,
                                         ctypes.c_void_p]),
 }
@@ -215,3 +217,7 @@ def ecc_bench_imad(threads, iters, sink, stream=None):
 
 def ecc_bench_modmul(curve, threads, iters, sink, stream=None):
     return _check(load().ecc_bench_modmul(curve, threads, iters, _ptr(sink), _stream(stream)))
+
+
+def ecc_bench_inv(curve, method, threads, iters, sink, stream=None):
+    return _check(load().ecc_bench_inv(curve, method, threads, iters, _ptr(sink), _stream(stream)))
