@@ -170,6 +170,14 @@ int ecc_msm_bases(void* handle, size_t num_vectors, const uint32_t* scalars, uin
                   void* stream);
 int ecc_bases_destroy(void* handle);
 
+/* Ragged MSMs over resident bases (the serving form): instance i is
+ * sum_j k_ij P_j over the first sizes[i] resident bases; its sizes[i] scalar
+ * rows follow those of instance i - 1 in `scalars`.  sizes: HOST array of num
+ * counts, each <= the handle's base count.  out: num points.  No host
+ * synchronisation inside (graph-capturable with device buffers). */
+int ecc_msm_bases_ragged(void* handle, size_t num, const uint64_t* sizes, const uint32_t* scalars,
+                         uint32_t* out, void* stream);
+
 /* Window width used for an n-point MSM, and the autotuner's override for the
  * size class floor(log2 n) (c = 0 restores the cost-model default). */
 int ecc_msm_window(ecc_curve_t curve, size_t n);

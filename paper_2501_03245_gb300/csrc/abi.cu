@@ -387,7 +387,37 @@ int ecc_msm_bases(void* handle, size_t num_vectors, const uint32_t* scalars, uin
   const int L = field_limbs(curve, 0);
   Arg S(scalars, std::max<uint64_t>(n, 1) * num_vectors * 32), O(out, num_vectors * 2 * L * 4);
   return with_args(name, st, {&S}, {&O}, [&]() {
-    return launch_msm_bases(handle, (uint32_t)num_vectors, static_cast<const uint32_t*>(S.dev),
+    return launch_msm_bases(handle, (uint32_t)num_vectors, nullptr, static_cast<const uint32_t*>(S.dev),
+                            static_cast<uint32_t*>(O.dev), st);
+  });
+}
+
+int ecc_msm_bases_ragged(void* handle, size_t num, const uint64_t* sizes, const uint32_t* scalars,
+                         uint32_t* out, void* stream) {
+  const char* name = "ecc_msm_bases_ragged";
+  if (!handle) return fail(ECC_EINVAL, "%s: NULL handle", name);
+  if (num == 0) return ok();
+  if (!sizes || !out) return fail(ECC_EINVAL, "%s: NULL pointer", name);
+  if (!host_memory(sizes)) return fail(ECC_EINVAL, "%s: sizes must be host memory", name);
+  if (num > (1u << 20)) return fail(ECC_EINVAL, "%s: num > 2^20", name);
+  const uint64_t n = bases_count(handle);
+  uint64_t rows = 0;
+  for (size_t i = 0; i < num; ++i) {
+    if (sizes[i] > n) return fail(ECC_EINVAL, "%s: sizes[%zu] exceeds the %llu resident bases", name, i,
+                                  (unsigned long long)n);
+    rows += sizes[i];
+  }
+  if (rows && !scalars) return fail(ECC_EINVAL, "%s: NULL pointer", name);
+  if ((scalars && !aligned4(scalars)) || !aligned4(out))
+    return fail(ECC_EINVAL, "%s: pointers must be 4-byte aligned", name);
+  const int curve = bases_curve(handle);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int L = field_limbs(curve, 0);
+  Arg S(scalars ? scalars : out, std::max<uint64_t>(rows, 1) * 32), O(out, num * 2 * L * 4);
+  std::vector<Arg*> ins;
+  if (rows) ins.push_back(&S);
+  return with_args(name, st, ins, {&O}, [&]() {
+    return launch_msm_bases(handle, (uint32_t)num, sizes, static_cast<const uint32_t*>(S.dev),
                             static_cast<uint32_t*>(O.dev), st);
   });
 }

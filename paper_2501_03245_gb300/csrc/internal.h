@@ -72,7 +72,8 @@ cudaError_t bases_create(int curve, uint64_t n, const uint32_t* points, void** h
 cudaError_t bases_destroy(void* handle);
 int bases_curve(void* handle);
 uint64_t bases_count(void* handle);
-cudaError_t launch_msm_bases(void* handle, uint32_t num_vectors, const uint32_t* scalars,
+cudaError_t launch_msm_bases(void* handle, uint32_t num_vectors, const uint64_t* sizes,
+                             const uint32_t* scalars,
                              uint32_t* out, cudaStream_t st);
 
 // benchmarks

@@ -13,9 +13,11 @@ cudaError_t msm_points_bn254(uint32_t num, const uint64_t* offsets, const uint32
                              const uint32_t* scalars, uint32_t* out, cudaStream_t st);
 cudaError_t msm_points_bls12_381(uint32_t num, const uint64_t* offsets, const uint32_t* points,
                                  const uint32_t* scalars, uint32_t* out, cudaStream_t st);
-cudaError_t msm_bases_bn254(void* bases, uint32_t num_vectors, const uint32_t* scalars,
+cudaError_t msm_bases_bn254(void* bases, uint32_t num_vectors, const uint64_t* sizes,
+                            const uint32_t* scalars,
                             uint32_t* out, cudaStream_t st);
-cudaError_t msm_bases_bls12_381(void* bases, uint32_t num_vectors, const uint32_t* scalars,
+cudaError_t msm_bases_bls12_381(void* bases, uint32_t num_vectors, const uint64_t* sizes,
+                                const uint32_t* scalars,
                                 uint32_t* out, cudaStream_t st);
 cudaError_t points_to_mont(int curve, const uint32_t* in, uint64_t n, uint32_t* out,
                            cudaStream_t st);
@@ -106,11 +108,12 @@ cudaError_t bases_destroy(void* handle) {
   return e;
 }
 
-cudaError_t launch_msm_bases(void* handle, uint32_t num_vectors, const uint32_t* scalars,
+cudaError_t launch_msm_bases(void* handle, uint32_t num_vectors, const uint64_t* sizes,
+                             const uint32_t* scalars,
                              uint32_t* out, cudaStream_t st) {
   switch (bases_curve(handle)) {
-    case 2: return msm_bases_bn254(handle, num_vectors, scalars, out, st);
-    case 3: return msm_bases_bls12_381(handle, num_vectors, scalars, out, st);
+    case 2: return msm_bases_bn254(handle, num_vectors, sizes, scalars, out, st);
+    case 3: return msm_bases_bls12_381(handle, num_vectors, sizes, scalars, out, st);
   }
   return cudaErrorNotSupported;
 }

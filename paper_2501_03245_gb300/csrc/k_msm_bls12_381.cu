@@ -9,9 +9,10 @@ cudaError_t msm_points_bls12_381(uint32_t num, const uint64_t* offsets, const ui
   return msm_detail::msm_points<BLS12_381>(3, num, offsets, points, scalars, out, st);
 }
 
-cudaError_t msm_bases_bls12_381(void* bases, uint32_t num_vectors, const uint32_t* scalars,
+cudaError_t msm_bases_bls12_381(void* bases, uint32_t num_vectors, const uint64_t* sizes,
+                                const uint32_t* scalars,
                                 uint32_t* out, cudaStream_t st) {
-  return msm_detail::msm_bases_t<BLS12_381>(static_cast<msm_detail::Bases*>(bases), num_vectors, scalars,
+  return msm_detail::msm_bases_t<BLS12_381>(static_cast<msm_detail::Bases*>(bases), num_vectors, sizes, scalars,
                                      out, st);
 }
 

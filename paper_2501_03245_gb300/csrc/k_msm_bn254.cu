@@ -12,9 +12,10 @@ cudaError_t msm_points_bn254(uint32_t num, const uint64_t* offsets, const uint32
   return msm_detail::msm_points<BN254>(2, num, offsets, points, scalars, out, st);
 }
 
-cudaError_t msm_bases_bn254(void* bases, uint32_t num_vectors, const uint32_t* scalars,
+cudaError_t msm_bases_bn254(void* bases, uint32_t num_vectors, const uint64_t* sizes,
+                            const uint32_t* scalars,
                             uint32_t* out, cudaStream_t st) {
-  return msm_detail::msm_bases_t<BN254>(static_cast<msm_detail::Bases*>(bases), num_vectors, scalars,
+  return msm_detail::msm_bases_t<BN254>(static_cast<msm_detail::Bases*>(bases), num_vectors, sizes, scalars,
                                      out, st);
 }
 

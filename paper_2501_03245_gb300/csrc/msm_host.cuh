@@ -214,10 +214,17 @@ struct Bases {
 };
 
 template <class C>
-cudaError_t msm_bases_t(Bases* bs, uint32_t num_vectors, const uint32_t* scalars, uint32_t* out,
-                        cudaStream_t st) {
+cudaError_t msm_bases_t(Bases* bs, uint32_t num_vectors, const uint64_t* vec_sizes,
+                        const uint32_t* scalars, uint32_t* out, cudaStream_t st) {
+  // instance v uses bases [0, size_v) and the scalar rows that follow the
+  // previous instances' (all n bases each when vec_sizes is null)
   std::vector<uint64_t> sizes(num_vectors, bs->n), poff(num_vectors, 0), soff(num_vectors);
-  for (uint32_t v = 0; v < num_vectors; ++v) soff[v] = (uint64_t)v * bs->n;
+  uint64_t acc = 0;
+  for (uint32_t v = 0; v < num_vectors; ++v) {
+    if (vec_sizes) sizes[v] = vec_sizes[v];
+    soff[v] = acc;
+    acc += sizes[v];
+  }
   Layout L = plan(bs->curve, num_vectors, sizes.data(), poff.data(), soff.data(), nullptr);
   return run_set<C>(bs->curve, L, bs->mont, scalars, out, st);
 }

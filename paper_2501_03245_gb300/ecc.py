@@ -47,6 +47,7 @@ _SIGS = {
     "ecc_msm_ragged": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t] + [ctypes.c_void_p] * 5),
     "ecc_bases_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t] + [ctypes.c_void_p] * 3),
     "ecc_msm_bases": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t] + [ctypes.c_void_p] * 3),
+    "ecc_msm_bases_ragged": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t] + [ctypes.c_void_p] * 4),
     "ecc_bases_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "ecc_msm_window": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t]),
     "ecc_msm_set_window": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
@@ -194,6 +195,15 @@ def ecc_bases_create(curve, n, points, stream=None):
 
 def ecc_msm_bases(handle, num_vectors, scalars, out, stream=None):
     return _check(load().ecc_msm_bases(handle, num_vectors, _ptr(scalars), _ptr(out), _stream(stream)))
+
+
+def ecc_msm_bases_ragged(handle, num, sizes, scalars, out, stream=None):
+    """sizes: host array (numpy uint64 or list) of num instance sizes."""
+    import numpy as np
+
+    sz = np.ascontiguousarray(np.asarray(sizes, dtype=np.uint64))
+    return _check(load().ecc_msm_bases_ragged(handle, num, sz.ctypes.data, _ptr(scalars), _ptr(out),
+                                              _stream(stream)))
 
 
 def ecc_bases_destroy(handle):
