@@ -11,6 +11,7 @@
 #include "internal.h"
 #include "msm.cuh"
 #include "scan.cuh"
+#include "upload.cuh"
 
 namespace ecc {
 
@@ -65,7 +66,7 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
   uint32_t* vals = reinterpret_cast<uint32_t*>(take(sz_kv));
   uint4* sbuf = reinterpret_cast<uint4*>(take(3 * sz_S));
   uint4* pbuf = reinterpret_cast<uint4*>(take(2 * sz_P));
-  e = cudaMemcpyAsync(d_inst, L.inst.data(), num * sizeof(MsmInst), cudaMemcpyHostToDevice, st);
+  e = upload_words(d_inst, L.inst.data(), num * sizeof(MsmInst), st);
   if (e != cudaSuccess) return e;
   // ---- 1-2: digits, counting sort by bucket id
   e = cudaMemsetAsync(count, 0, (B + 1) * 4, st);
@@ -124,7 +125,7 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
     char* q = rs.as<char>();
     uint32_t* d_ids = reinterpret_cast<uint32_t*>(q);
     q += up(n_inst * 4);
-    e = cudaMemcpyAsync(d_ids, ids.data(), n_inst * 4, cudaMemcpyHostToDevice, st);
+    e = upload_words(d_ids, ids.data(), n_inst * 4, st);
     if (e != cudaSuccess) return e;
     const Jac<F>* in_R = nullptr;
     const Jac<F>* in_S = nullptr;
