@@ -98,6 +98,28 @@ int ecc_fp_inv(ecc_curve_t curve, int field, size_t n, const uint32_t* a, uint32
 int ecc_fp_inv_batch(ecc_curve_t curve, int field, size_t n, const uint32_t* a, uint32_t* out,
                      void* stream);
 
+/* Allocation-free variant of ecc_fp_inv_batch (this entry point has no
+ * counterpart in the paper).  It is for callers that may not allocate device
+ * memory during a call: a service that fixes its memory budget at start-up and
+ * forbids later allocation, a latency-critical loop that cannot afford the
+ * device-wide synchronisation cudaMalloc implies, or a host library without an
+ * allocator of its own.  It calls no cudaMalloc, cudaFree or allocating library
+ * routine: its scratch is a fixed device array inside the library, sized for
+ * n <= 65536 elements of any field (9 MiB, held by every GPU that loads the
+ * library until the process exits); larger n returns ECC_EINVAL.
+ *   - a, out: DEVICE memory only (host buffers would need a staging
+ *     allocation: ECC_EINVAL); same layout and results as ecc_fp_inv_batch.
+ *   - The first call on a device looks up the scratch array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the one scratch array: calls that overlap on the GPU
+ *     (different streams, or several host threads) race and corrupt each
+ *     other's results; serialise them, e.g. on one stream.  No part of the
+ *     scratch needs clearing between calls: every word is written before it is
+ *     read. */
+int ecc_fp_inv_batch_noalloc(ecc_curve_t curve, int field, size_t n, const uint32_t* a,
+                             uint32_t* out, void* stream);
+
 /* ---------------------------------------------------------------- EC operators
  * out[i] = p[i] + q[i] (batched affine PADD, Section 3.3, Eqn 2-3; PDBL when
  * p[i] = q[i]; O and p[i] = -q[i] follow the group law).  Points must be on the

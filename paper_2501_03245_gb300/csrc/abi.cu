@@ -457,6 +457,25 @@ int ecc_bench_modmul(ecc_curve_t curve, size_t threads, int iters, uint32_t* sin
   return ok();
 }
 
+int ecc_fp_inv_batch_noalloc(ecc_curve_t curve, int field, size_t n, const uint32_t* a,
+                             uint32_t* out, void* stream) {
+  const char* name = "ecc_fp_inv_batch_noalloc";
+  if (!valid_curve(curve)) return fail(ECC_EINVAL, "%s: unknown curve %d", name, (int)curve);
+  if (field != 0 && field != 1) return fail(ECC_EINVAL, "%s: field must be 0 or 1", name);
+  if (n == 0) return ok();
+  if (n > kNoAllocMaxElems)
+    return fail(ECC_EINVAL, "%s: n = %zu exceeds the fixed scratch capacity of %zu elements", name, n,
+                kNoAllocMaxElems);
+  if (!a || !out) return fail(ECC_EINVAL, "%s: NULL pointer", name);
+  if (!aligned4(a) || !aligned4(out)) return fail(ECC_EINVAL, "%s: pointers must be 4-byte aligned", name);
+  if (host_memory(a) || host_memory(out))
+    return fail(ECC_EINVAL, "%s: a and out must be device memory (staging host buffers would allocate)",
+                name);
+  cudaError_t e = launch_fe_inv_batch_noalloc(curve, field, n, a, out, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, name);
+  return ok();
+}
+
 int ecc_bench_inv(ecc_curve_t curve, int method, size_t threads, int iters, uint32_t* sink,
                   void* stream) {
   if (!valid_curve(curve)) return fail(ECC_EINVAL, "ecc_bench_inv: unknown curve");

@@ -42,6 +42,11 @@ cudaError_t launch_fe_inv(int curve, int field, size_t n, const uint32_t* a, uin
 cudaError_t launch_fe_inv_batch(int curve, int field, size_t n, const uint32_t* a, uint32_t* out,
                                 cudaStream_t st);
 int field_limbs(int curve, int field);
+// Allocation-free batch inversion: scratch is a fixed device array sized for
+// kNoAllocMaxElems elements; a, out must be device memory.
+constexpr size_t kNoAllocMaxElems = (size_t)1 << 16;
+cudaError_t launch_fe_inv_batch_noalloc(int curve, int field, size_t n, const uint32_t* a,
+                                        uint32_t* out, cudaStream_t st);
 
 // EC operators
 cudaError_t launch_point_add(int curve, size_t n, const uint32_t* p, const uint32_t* q,

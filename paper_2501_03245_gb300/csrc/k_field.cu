@@ -1,11 +1,41 @@
 // Field-layer kernels and launchers: modmul / modadd / modinv unit operations,
 // batch inversion, and the integer multiply-add issue-rate probes.
+#include <mutex>
+
 #include "internal.h"
 #include "ops.cuh"
 
 namespace ecc {
 
+// Fixed device scratch of the allocation-free batch inversion: the input,
+// output and prefix-product arrays of up to kNoAllocMaxElems elements of the
+// widest field (12 limbs).  Every GPU that loads the library holds it
+// (3 x 65536 x 48 B = 9 MiB) until the process exits.
+static __device__ __align__(256) uint32_t g_noalloc_scratch[3 * kNoAllocMaxElems * 12];
+
 namespace {
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[64] = {};
+
+// Device address of the scratch array on the current device.  In host code the
+// array's name is only a host-side stand-in, so the address is looked up once per
+// device with that device current.
+cudaError_t noalloc_scratch(void** ptr) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_addr[dev] = p;
+  }
+  *ptr = g_noalloc_addr[dev];
+  return cudaSuccess;
+}
 
 template <class F>
 cudaError_t fe_ops(int op, size_t n, const uint32_t* a, const uint32_t* b, uint32_t* out,
@@ -67,6 +97,31 @@ __global__ void k_bench_modmul(int iters, uint32_t* sink) {
 #pragma unroll
     for (int k = 0; k < N; ++k) acc ^= x[c][k];
   sink[t] = acc;
+}
+
+// Batch inversion into caller-free scratch: the same three kernels as
+// fe_inv_batch, with the in / out / prefix arrays carved from the file-scope
+// device array below instead of a stream-ordered allocation.
+template <class F>
+cudaError_t fe_inv_batch_noalloc(void* scratch, size_t n, const uint32_t* a, uint32_t* out,
+                                 cudaStream_t st) {
+  constexpr int B = kBlock;
+  const size_t soa = soa_bytes<F>(n);
+  uint4* base = static_cast<uint4*>(scratch);
+  SoA<F> in{base, n}, res{base + soa / 16, n}, M{base + 2 * soa / 16, n};
+  const unsigned cb = (unsigned)((n + 255) / 256);
+  k_fe_in<F><<<cb, 256, 0, st>>>(a, n, F::N, 0, in, 1);
+  size_t ctas = (size_t)device_sm_count() * kGasCtasPerSm;
+  size_t per = (n + ctas - 1) / ctas;
+  if (per < B) per = B;
+  ctas = (n + per - 1) / per;
+  const size_t smem = sizeof(GasSmem<F::N, B>);
+  cudaError_t e = cudaFuncSetAttribute(k_batch_inverse<F, B>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_batch_inverse<F, B><<<(unsigned)ctas, B, smem, st>>>(in, res, M, n, per);
+  k_fe_out<F><<<cb, 256, 0, st>>>(res, n, out, F::N, 0, 1);
+  return cudaGetLastError();
 }
 
 // a chain of `iters` dependent inversions per thread: method 0 Fermat, 1 divsteps
@@ -154,6 +209,14 @@ cudaError_t launch_fe_inv(int curve, int field, size_t n, const uint32_t* a, uin
 cudaError_t launch_fe_inv_batch(int curve, int field, size_t n, const uint32_t* a, uint32_t* out,
                                 cudaStream_t st) {
   ECC_FIELD_DISPATCH(curve, field, (fe_inv_batch<F>(n, a, out, st)))
+}
+
+cudaError_t launch_fe_inv_batch_noalloc(int curve, int field, size_t n, const uint32_t* a,
+                                        uint32_t* out, cudaStream_t st) {
+  void* scratch = nullptr;
+  cudaError_t e = noalloc_scratch(&scratch);
+  if (e != cudaSuccess) return e;
+  ECC_FIELD_DISPATCH(curve, field, (fe_inv_batch_noalloc<F>(scratch, n, a, out, st)))
 }
 
 cudaError_t launch_bench_imad(size_t threads, int iters, uint32_t* sink, cudaStream_t st) {

@@ -38,6 +38,8 @@ _SIGS = {
     "ecc_fp_sub": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_size_t] + [ctypes.c_void_p] * 4),
     "ecc_fp_inv": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_size_t] + [ctypes.c_void_p] * 3),
     "ecc_fp_inv_batch": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_size_t] + [ctypes.c_void_p] * 3),
+    "ecc_fp_inv_batch_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_size_t] +
+                                 [ctypes.c_void_p] * 3),
     "ecc_point_add_batch": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t] + [ctypes.c_void_p] * 4),
     "ecc_point_dbl_batch": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t] + [ctypes.c_void_p] * 3),
     "ecc_verify_batch": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t] + [ctypes.c_void_p] * 6),
@@ -149,6 +151,12 @@ def ecc_fp_inv(curve, field, n, a, out, stream=None):
 
 def ecc_fp_inv_batch(curve, field, n, a, out, stream=None):
     return _check(load().ecc_fp_inv_batch(curve, field, n, _ptr(a), _ptr(out), _stream(stream)))
+
+
+def ecc_fp_inv_batch_noalloc(curve, field, n, a, out, stream=None):
+    """Allocation-free batch inversion (device buffers only, n <= 65536)."""
+    return _check(load().ecc_fp_inv_batch_noalloc(curve, field, n, _ptr(a), _ptr(out),
+                                                  _stream(stream)))
 
 
 def ecc_point_add_batch(curve, n, p, q, out, stream=None):
