@@ -22,6 +22,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -38,6 +40,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=N_VERIFY, help="triples per rank (default 2^20)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-msm", action="store_true", help="skip the MSM and ragged-MSM lines")
     return ap.parse_args()
 
 
@@ -164,6 +167,97 @@ def cpu_baseline_verify(e, r, s, pub, sample):
     return {"value": sample / dt, "unit": "verifies/s", "cores": threads, "kind": "oracle",
             "sample": f"first {sample} of the 2^20 P-256 triples, plain C++ bigint oracle "
                       f"(Barrett + Jacobian), {threads} threads, {dt:.2f} s"}
+
+
+BLS_R = 0x73EDA753299D7D483339D80809A1D80553BDA402FFFE5BFEFFFFFFFF00000001
+BN_R = 0x30644E72E131A029B85045B68181585D2833E84879B9709143E1F593F0000001
+
+
+def _event_time(torch, fn, reps):
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / 1e3 / reps
+
+
+def bench_msm(ecc, costmodel, synth, torch, peak, rank):
+    """BLS12-381 MSM: 2^20 resident bases a_i G, 16 scalar vectors per step
+    (one ecc_msm_bases call), against the plain form (one MSM launch sequence
+    per vector)."""
+    n, V, curve = 1 << 20, 16, ecc.ECC_BLS12_381
+    seed = synth.SEED_BASE + 2 + 1000 * rank
+    a, ks = synth.msm_raw(seed, n, BLS_R, V)
+    pts = torch.empty((n, 24), dtype=torch.int32, device="cuda")
+    ecc.ecc_fixed_base_mul(curve, n, torch.from_numpy(a.view("int32")).cuda(), pts)
+    sc = torch.from_numpy(np.concatenate(ks).view("int32")).cuda()
+    h = ecc.ecc_bases_create(curve, n, pts)
+    out = torch.empty((V, 24), dtype=torch.int32, device="cuda")
+    try:
+        ecc.ecc_msm_bases(h, V, sc, out)
+        t = _event_time(torch, lambda: ecc.ecc_msm_bases(h, V, sc, out), 2)
+        one = out[:1]
+        t1 = _event_time(torch, lambda: [ecc.ecc_msm_bases(h, 1, sc[v * n:(v + 1) * n], one)
+                                         for v in range(V)], 1)
+    finally:
+        ecc.ecc_bases_destroy(h)
+    c = ecc.ecc_msm_window(curve, n)
+    W = -(-256 // c)
+    alg = costmodel.msm_modmul(n, W, c) * V * costmodel.imad_per_modmul(12)
+    return {"workload": "MSM BLS12-381 G1, 2^20 resident bases, 16 scalar vectors per step",
+            "value": n * V / t, "unit": "points/s", "ms_per_step": t * 1e3, "window_c": c,
+            "plain": {"value": n * V / t1, "unit": "points/s",
+                      "form": "one MSM launch sequence per scalar vector"},
+            "roofline": {"bound": "alu", "achieved": alg / t / 1e12, "peak": peak / 1e12,
+                         "unit": "T IMAD.WIDE/s", "frac": alg / t / peak,
+                         "basis": "6 modmul per (point, window) digit + 2 PADD per bucket + "
+                                  "window combination, 300 wide mul-adds per modmul"}}
+
+
+def bench_ragged(ecc, synth, torch, rank):
+    """BN254 ragged batch: 256 MSMs with log-uniform sizes 2^10..2^18, all in one
+    launch sequence captured once in a CUDA graph and replayed, against one
+    launch sequence per MSM."""
+    curve = ecc.ECC_BN254
+    seed = synth.SEED_BASE + 3 + 1000 * rank
+    sizes = synth.ragged_sizes(seed, 256)
+    total = int(sizes.sum())
+    a, ks = synth.msm_raw(seed, total, BN_R, 1)
+    pts = torch.empty((total, 16), dtype=torch.int32, device="cuda")
+    ecc.ecc_fixed_base_mul(curve, total, torch.from_numpy(a.view("int32")).cuda(), pts)
+    sc = torch.from_numpy(ks[0].view("int32")).cuda()
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    out = torch.empty((256, 16), dtype=torch.int32, device="cuda")
+    ecc.ecc_msm_ragged(curve, 256, offs, pts, sc, out)
+    torch.cuda.synchronize()
+    eager = _event_time(torch, lambda: ecc.ecc_msm_ragged(curve, 256, offs, pts, sc, out), 2)
+    graph = None
+    try:
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            ecc.ecc_msm_ragged(curve, 256, offs, pts, sc, out, s)  # warm inside the side stream
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            ecc.ecc_msm_ragged(curve, 256, offs, pts, sc, out, s)
+        ref = out.clone()
+        graph = _event_time(torch, g.replay, 3)
+        graph_ok = bool(torch.equal(out, ref))
+    except Exception as ex:  # report, keep the eager number
+        graph_ok = f"capture failed: {ex}"
+    one = torch.empty((1, 16), dtype=torch.int32, device="cuda")
+    per = _event_time(torch, lambda: [ecc.ecc_msm(curve, int(sizes[i]), pts[int(offs[i]):int(offs[i + 1])],
+                                                  sc[int(offs[i]):int(offs[i + 1])], one)
+                                      for i in range(256)], 1)
+    best = graph if graph else eager
+    return {"workload": "256 BN254 MSMs, sizes log-uniform 2^10..2^18, one launch sequence",
+            "points": total, "value": total / best, "unit": "points/s",
+            "graph_replay_ms": graph * 1e3 if graph else None, "eager_ms": eager * 1e3,
+            "graph_bit_equal": graph_ok,
+            "plain": {"value": total / per, "unit": "points/s", "form": "one launch sequence per MSM"}}
 
 
 def run_reference(args):
@@ -293,6 +387,10 @@ def run_ours(args):
     torch.cuda.synchronize()
     plain = plain_n / (a.elapsed_time(b) / 1e3)
 
+    cpu_baseline = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu_baseline = cpu_baseline_verify(e.cpu().numpy(), r.cpu().numpy(), s.cpu().numpy(),
+                                           pub.cpu().numpy(), 16384)
     peak = imad_peak(ecc, torch, sms)
     alg = costmodel.verify_imad() * n
     launch_s = statistics.median(per_launch)
@@ -316,9 +414,12 @@ def run_ours(args):
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
     }
+    del e, r, s, pub, ok, e_h, r_h, s_h, p_h, ok_h
+    if not args.no_msm:
+        line["msm"] = bench_msm(ecc, costmodel, synth, torch, peak, rank)
+        line["ragged"] = bench_ragged(ecc, synth, torch, rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_verify(e.cpu().numpy(), r.cpu().numpy(),
-                                                   s.cpu().numpy(), pub.cpu().numpy(), 16384)
+        line["cpu_baseline"] = cpu_baseline
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -30,35 +30,49 @@ struct Trans {
   int64_t u, v, q, r;
 };
 
+ECC_DEV int ctz64(uint64_t x) {
+#ifdef __CUDA_ARCH__
+  return __ffsll((long long)x) - 1;
+#else
+  return __builtin_ctzll(x);
+#endif
+}
+
 // 62 divsteps on the low bits of f and g (f odd).  delta is carried across calls.
+// A run of k divsteps with g even (g <- g/2, delta <- delta + 1) is applied at
+// once by counting trailing zeros; only odd-g steps go one at a time.
 ECC_DEV Trans divsteps62(int64_t& delta, uint64_t f, uint64_t g) {
   int64_t u = 1, v = 0, q = 0, r = 1;
-  for (int i = 0; i < 62; ++i) {
-    if (g & 1) {
-      if (delta > 0) {
-        delta = 1 - delta;
-        const uint64_t nf = g;
-        g = (g - f) >> 1;
-        f = nf;
-        const int64_t nu = 2 * q, nv = 2 * r;
-        q = q - u;
-        r = r - v;
-        u = nu;
-        v = nv;
-      } else {
-        delta = 1 + delta;
-        g = (g + f) >> 1;
-        q = q + u;
-        r = r + v;
-        u = 2 * u;
-        v = 2 * v;
-      }
+  int left = 62;
+  for (;;) {
+    // the bit at position `left` keeps the count finite when g's low bits are 0
+    int z = ctz64(g | ((uint64_t)1 << left));
+    g >>= z;
+    u <<= z;
+    v <<= z;
+    delta += z;
+    left -= z;
+    if (left == 0) break;
+    // g odd: one divstep
+    if (delta > 0) {
+      delta = 1 - delta;
+      const uint64_t nf = g;
+      g = (g - f) >> 1;
+      f = nf;
+      const int64_t nu = 2 * q, nv = 2 * r;
+      q = q - u;
+      r = r - v;
+      u = nu;
+      v = nv;
     } else {
       delta = 1 + delta;
-      g >>= 1;
+      g = (g + f) >> 1;
+      q = q + u;
+      r = r + v;
       u = 2 * u;
       v = 2 * v;
     }
+    if (--left == 0) break;
   }
   return Trans{u, v, q, r};
 }
