@@ -13,10 +13,12 @@
 //      trick with GAS, Section 3.2).  A chunk entry that starts a new bucket
 //      flushes the running sum as a partial bucket sum and restarts it (a copy,
 //      no inversion needed).  CH rounds finish the whole array in one launch;
-//   4. bucket reduction sum_k k B_k per window by chunked running sums and
-//   5. window combination sum_w 2^(c w) S_w, both in Jacobian coordinates
-//      (long dependent chains with little parallelism, where a batch inversion
-//      per step would be pure latency).
+//   4. bucket reduction sum_k k B_k per window by chunked running sums: the
+//      first level (many independent chunks) as batched affine additions, the
+//      short upper levels in Jacobian coordinates;
+//   5. window combination sum_w 2^(c w) S_w in Jacobian coordinates (one long
+//      dependent chain per instance, where a batch inversion per step would be
+//      pure latency).
 // Several independent MSM instances (different sizes, windows and bases) run
 // through the same launches: every instance owns a disjoint range of bucket ids.
 #pragma once
@@ -156,6 +158,7 @@ struct AccArgs {
   const uint32_t* bases;  // AoS Montgomery affine points, 2N words each
   PtSoA<F> S;             // running sum per chunk
   PtSoA<F> partial;       // partial bucket sums
+  uint32_t* slot_bucket;  // bucket of every partial slot
   SoA<F> M;
   uint64_t per_cta;
 };
@@ -224,7 +227,9 @@ struct AccRound {
     if (start) {
       if (j > 0) {
         a->S.load(c, xs, ys);
-        a->partial.store(partial_slot(*a, prev, c), xs, ys);
+        const uint64_t ps = partial_slot(*a, prev, c);
+        a->partial.store(ps, xs, ys);
+        a->slot_bucket[ps] = prev;
       }
       a->S.store(c, xp, yp);
     } else {
@@ -258,104 +263,411 @@ __global__ void __launch_bounds__(BLOCK, kGasResidentThreads / BLOCK) k_msm_accu
     const uint32_t key = a.keys[(uint64_t)jl * a.n_chunks + c];
     uint32_t xs[N], ys[N];
     a.S.load(c, xs, ys);
-    a.partial.store(partial_slot(a, key, c), xs, ys);
+    const uint64_t ps = partial_slot(a, key, c);
+    a.partial.store(ps, xs, ys);
+    a.slot_bucket[ps] = key;
   }
 }
 
 // ------------------------------------------------------------------ reduction
+//
+// Window sum sum_b b E_b (E_b the bucket sums, b = 1 .. 2^(c-1)) in levels.
+// Level 1 cuts each window row into chunks of kRedChunk1 consecutive buckets;
+// chunk u (buckets lo .. hi-1, 0-based) yields the plain sum R_u and the sum
+// S_u = sum_e (e - lo + 1) E_e weighted from the chunk's own first bucket, so
+// the window sum is sum_u (S_u + u (kRedChunk1 R_u)).  Every later level takes
+// elements (R~_e, S~_e) whose target is sum_e (S~_e + e R~_e) and cuts them
+// into chunks of kRedChunkN: chunk v yields R_v = sum R~_e and
+// S_v = sum_e (S~_e + (e - lo) R~_e), and hands (kRedChunkN R_v, S_v) on, until
+// one element per row is left: its S is the window sum.  The multiples of R are
+// taken by the producing level (log2 of the chunk size doublings per output).
+//
+// Before level 1 the partial sums of every bucket are folded into one (a
+// batched affine pairwise tree, ceil(log2 k) rounds for k partials; CTAs take
+// equal shares of the partial slots, so a bucket holding many entries costs
+// rounds only in the CTA that owns it).  Level 1 then has 2^(c-1) / kRedChunk1
+// independent chunks per window row and runs as batched affine additions
+// (Section 3.3) with one inversion per CTA per round (Section 3.2): the running
+// sums R and S of every chunk walk the chunk's buckets downwards, adding the
+// bucket sum to R ("A" event) and then R to S ("S" event).  An S event uses
+// the R of before the next bucket's A event, so the two share a round and a
+// chunk of k buckets takes k + 1 rounds.  The short upper levels run in
+// Jacobian coordinates, one thread per chunk.
 
-// Weighted chunk sums.  Elements e = lo .. hi of one window carry (R_e, S_e)
-// with R the plain sum and S the sum weighted from the element's own first
-// bucket; span is the bucket count of one element.  The chunk returns
-// R = sum R_e and S = sum S_e + span * sum_e (e - lo) R_e, so that the window
-// sum is sum over chunks of S + (first bucket - 1) R.
-template <class C>
-struct ReduceArgs {
-  using F = typename C::Fp;
-  const MsmInst* inst;     // instances of this group (same c and W)
-  const uint32_t* inst_ids;
-  uint32_t n_inst;
-  uint32_t W;
-  uint32_t elems;          // elements per window at this level
-  uint32_t chunk;          // elements per output chunk
-  uint32_t log_span;       // span = 2^log_span buckets per element
-  // level 1 reads buckets from the partial sums
-  const uint32_t* poff;
-  PtSoA<F> partial;
-  // other levels read (R, S) pairs written by the previous level
-  const Jac<F>* in_R;
-  const Jac<F>* in_S;
-  Jac<F>* out_R;
-  Jac<F>* out_S;
+constexpr uint32_t kRedChunk1 = 32;      // buckets per first-level chunk
+constexpr int kRedLog1 = 5;
+constexpr uint32_t kRedChunkN = 4;       // elements per chunk on the later levels
+constexpr int kRedLogN = 2;
+
+// First-level items (chunks) in group-major order: the items of one instance
+// are [t0, t0 + W * chunks), window row w first, then chunk u.
+struct RedRange {
+  uint64_t t0;
+  uint32_t inst;
+  uint32_t chunks;  // chunks per window row
 };
 
+// ---- fold: the partial sums of every bucket into its first partial slot
 template <class C>
-ECC_DEV void bucket_sum(const ReduceArgs<C>& a, uint32_t b, Jac<typename C::Fp>& B) {
+struct FoldArgs {
+  using F = typename C::Fp;
+  const uint32_t* poff;         // partial-slot offsets per bucket (n_buckets + 1)
+  uint32_t n_buckets;
+  const uint32_t* slot_bucket;  // bucket of every partial slot
+  PtSoA<F> partial;
+  SoA<F> M;                     // GAS prefix products, one per slot
+};
+
+// first b in [0, n] with poff[b] >= x
+ECC_DEV uint32_t lower_bound_u32(const uint32_t* v, uint32_t n, uint64_t x) {
+  uint32_t lo = 0, hi = n;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (v[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// Round with stride h: slot l of a bucket with k partials adds slot l + h when
+// l is a multiple of 2h and l + h < k.
+template <class C>
+struct FoldOp {
+  using F = typename C::Fp;
+  static constexpr int N = F::N;
+  const FoldArgs<C>* a;
+  uint32_t h;
+  ECC_DEV bool active(uint64_t s) const {
+    const uint32_t b = a->slot_bucket[s];
+    const uint32_t l = (uint32_t)(s - a->poff[b]), k = a->poff[b + 1] - a->poff[b];
+    return (l & (2 * h - 1)) == 0 && l + h < k;
+  }
+  ECC_DEV int den(uint64_t s, uint32_t* d) const {
+    uint32_t x0[N], y0[N], x1[N], y1[N];
+    a->partial.load(s, x0, y0);
+    a->partial.load(s + h, x1, y1);
+    return add_den<C>(d, x0, y0, x1, y1);
+  }
+  ECC_DEV void finish(uint64_t s, int kind, const uint32_t* inv) const {
+    uint32_t x0[N], y0[N], x1[N], y1[N];
+    a->partial.load(s, x0, y0);
+    a->partial.load(s + h, x1, y1);
+    add_finish<C>(x0, y0, kind, inv, x0, y0, x1, y1);
+    a->partial.store(s, x0, y0);
+  }
+};
+
+template <class C, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, kGasResidentThreads / BLOCK) k_msm_fold(FoldArgs<C> a) {
   using F = typename C::Fp;
   constexpr int N = F::N;
-  jac_set_inf<C>(B);
-  const uint32_t lo = a.poff[b], hi = a.poff[b + 1];
-  for (uint32_t s = lo; s < hi; ++s) {
-    uint32_t x[N], y[N];
-    a.partial.load(s, x, y);
-    jac_add_mixed<C>(B, B, x, y);
+  auto& sm = gas_smem<N, BLOCK>();
+  const uint64_t total = a.poff[a.n_buckets];
+  if (total == 0) return;  // uniform over the grid
+  // this CTA owns the buckets whose first slot lies in its equal share
+  const uint64_t share = (total + gridDim.x - 1) / gridDim.x;
+  const uint32_t b0 = lower_bound_u32(a.poff, a.n_buckets, blockIdx.x * share);
+  const uint32_t b1 = blockIdx.x + 1 == gridDim.x
+                          ? a.n_buckets
+                          : lower_bound_u32(a.poff, a.n_buckets, (blockIdx.x + 1) * share);
+  const uint64_t s0 = a.poff[b0], s1 = b1 > b0 ? a.poff[b1] : s0;
+  uint32_t kmax = 0;
+  for (uint64_t s = s0 + threadIdx.x; s < s1; s += BLOCK) {
+    const uint32_t b = a.slot_bucket[s];
+    const uint32_t k = a.poff[b + 1] - a.poff[b];
+    kmax = k > kmax ? k : kmax;
+  }
+  // ceil(log2 kmax) rounds; each halves the partials of every bucket
+  for (uint32_t h = 1; __syncthreads_or(h < kmax); h *= 2) {
+    FoldOp<C> op{&a, h};
+    uint32_t run[N];
+    fe_set_one<F>(run);
+    for (uint64_t s = s0 + threadIdx.x; s < s1; s += BLOCK) {
+      if (!op.active(s)) continue;
+      uint32_t d[N];
+      a.M.store(s, run);
+      op.den(s, d);
+      mont_mul<F>(run, run, d);
+    }
+    uint32_t inv[N];
+    cta_invert<F, BLOCK>(inv, run, sm);
+    if (s0 + threadIdx.x < s1) {
+      const uint64_t first = s0 + threadIdx.x;
+      const uint64_t last = first + ((s1 - 1 - first) / BLOCK) * BLOCK;
+      for (uint64_t s = last + BLOCK; s > first;) {
+        s -= BLOCK;
+        if (!op.active(s)) continue;
+        uint32_t d[N], pre[N], mine[N];
+        const int kind = op.den(s, d);
+        a.M.load(s, pre);
+        mont_mul<F>(mine, inv, pre);
+        mont_mul<F>(inv, inv, d);
+        op.finish(s, kind, mine);
+      }
+    }
   }
 }
 
 template <class C>
-__global__ void k_msm_reduce(ReduceArgs<C> a, int level1) {
+struct AffRedArgs {
   using F = typename C::Fp;
-  const uint32_t chunks = (a.elems + a.chunk - 1) / a.chunk;
+  const MsmInst* inst;
+  const RedRange* ranges;
+  uint32_t n_ranges;
+  uint64_t items;
+  const uint32_t* poff;   // partial-slot offsets per bucket (n_buckets + 1 entries)
+  PtSoA<F> partial;       // partial bucket sums (affine)
+  PtSoA<F> R, S;          // running sums per item (affine)
+  SoA<F> M;               // GAS prefix products per item
+  uint32_t* cur_e;        // 1 + the bucket the next event belongs to
+  uint32_t* cur_a;        // whether that bucket's A event is done
+  uint32_t* lo_b;         // first bucket of the item
+  Jac<F>* out_R;          // kRedChunk1 R per item (Jacobian, Z = 1 or O)
+  Jac<F>* out_S;
+  uint64_t per_cta;
+};
+
+ECC_DEV uint32_t find_range(const RedRange* r, uint32_t num, uint64_t t) {
+  uint32_t lo = 0, hi = num - 1;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) >> 1;
+    if (r[mid].t0 <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// The events of this round for an item at (ep, ad): ep = 1 + the current
+// bucket, ad = whether its A event is done.  An S event (S += R) and/or an A
+// event (R += bucket sum, held in the bucket's first partial slot after the
+// fold); (ep2, ad2) is the position after them.
+struct RedStep {
+  bool opS, opA;
+  uint32_t slot, ep2, ad2;
+};
+
+ECC_DEV RedStep red_step(const uint32_t* poff, uint32_t ep, uint32_t ad, uint32_t lo) {
+  RedStep r{false, false, 0u, ep, ad};
+  if (ep == lo) return r;                          // every event done
+  if (!ad) {
+    r.ad2 = 1;
+    if (poff[ep] > poff[ep - 1]) {                 // bucket ep-1 is not empty
+      r.opA = true;
+      r.slot = poff[ep - 1];
+      return r;
+    }
+  }
+  r.opS = true;                                    // bucket ep-1 is complete
+  r.ep2 = ep - 1;
+  r.ad2 = 0;
+  if (r.ep2 != lo) {
+    r.ad2 = 1;
+    if (poff[r.ep2] > poff[r.ep2 - 1]) {
+      r.opA = true;
+      r.slot = poff[r.ep2 - 1];
+    }
+  }
+  return r;
+}
+
+template <class C>
+struct AffRedRound {
+  using F = typename C::Fp;
+  static constexpr int N = F::N;
+  static constexpr int OPS = 2;  // op 0: S += R, op 1: R += partial
+  const AffRedArgs<C>* a;
+  RedStep st;
+  int kind_s, kind_a;
+  bool more;
+  ECC_DEV void den_c(size_t i, int j, uint32_t* d) {
+    if (j == 0) {
+      st = red_step(a->poff, a->cur_e[i], a->cur_a[i], a->lo_b[i]);
+      if (!st.opS) {
+        fe_set_one<F>(d);
+        kind_s = ADD_RET_T;
+        return;
+      }
+      uint32_t xs[N], ys[N], xr[N], yr[N];
+      a->S.load(i, xs, ys);
+      a->R.load(i, xr, yr);
+      kind_s = add_den<C>(d, xs, ys, xr, yr);
+    } else {
+      if (!st.opA) {
+        fe_set_one<F>(d);
+        kind_a = ADD_RET_T;
+        return;
+      }
+      uint32_t xr[N], yr[N], xp[N], yp[N];
+      a->R.load(i, xr, yr);
+      a->partial.load(st.slot, xp, yp);
+      kind_a = add_den<C>(d, xr, yr, xp, yp);
+    }
+  }
+  ECC_DEV void den_d(size_t i, int j, uint32_t* d) { den_c(i, j, d); }
+  ECC_DEV void finish(size_t i, const uint32_t (*inv)[N]) {
+    if (!st.opS && !st.opA) return;
+    uint32_t xr[N], yr[N];
+    a->R.load(i, xr, yr);
+    if (st.opS) {
+      uint32_t xs[N], ys[N];
+      a->S.load(i, xs, ys);
+      add_finish<C>(xs, ys, kind_s, inv[0], xs, ys, xr, yr);
+      a->S.store(i, xs, ys);
+    }
+    if (st.opA) {
+      uint32_t xp[N], yp[N];
+      a->partial.load(st.slot, xp, yp);
+      add_finish<C>(xr, yr, kind_a, inv[1], xr, yr, xp, yp);
+      a->R.store(i, xr, yr);
+    }
+    a->cur_e[i] = st.ep2;
+    a->cur_a[i] = st.ad2;
+    more |= st.ep2 != a->lo_b[i];
+  }
+};
+
+// R <- 2 R for every item (batched PDBL)
+template <class C>
+struct AffDblRound {
+  using F = typename C::Fp;
+  static constexpr int N = F::N;
+  static constexpr int OPS = 1;
+  const AffRedArgs<C>* a;
+  bool live;
+  ECC_DEV void den_c(size_t i, int, uint32_t* d) {
+    uint32_t x[N], y[N];
+    a->R.load(i, x, y);
+    live = dbl_den<C>(d, y);
+  }
+  ECC_DEV void den_d(size_t i, int j, uint32_t* d) { den_c(i, j, d); }
+  ECC_DEV void finish(size_t i, const uint32_t (*inv)[N]) {
+    uint32_t x[N], y[N];
+    a->R.load(i, x, y);
+    dbl_finish<C>(x, y, live, inv[0], x, y);
+    a->R.store(i, x, y);
+  }
+};
+
+template <class C, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, kGasResidentThreads / BLOCK)
+    k_msm_reduce_affine(AffRedArgs<C> a) {
+  using F = typename C::Fp;
+  constexpr int N = F::N;
+  auto& sm = gas_smem<N, BLOCK>();
+  const uint64_t begin = blockIdx.x * a.per_cta;
+  uint64_t end = begin + a.per_cta;
+  if (end > a.items) end = a.items;
+  if (end < begin) end = begin;
+  // start every item at the top of its chunk with R = S = O
+  bool more = false;
+  for (uint64_t t = begin + threadIdx.x; t < end; t += BLOCK) {
+    const RedRange rg = a.ranges[find_range(a.ranges, a.n_ranges, t)];
+    const MsmInst in = a.inst[rg.inst];
+    const uint32_t B = 1u << (in.c - 1);
+    const uint64_t local = t - rg.t0;
+    const uint32_t w = (uint32_t)(local / rg.chunks), u = (uint32_t)(local % rg.chunks);
+    const uint32_t lo = in.bucket_base + w * B + u * kRedChunk1;
+    const uint32_t hi = lo + (B - u * kRedChunk1 < kRedChunk1 ? B - u * kRedChunk1 : kRedChunk1);
+    a.lo_b[t] = lo;
+    a.cur_e[t] = hi;
+    a.cur_a[t] = 0;
+    uint32_t z[N];
+    fe_set_zero<F>(z);
+    a.R.store(t, z, z);
+    a.S.store(t, z, z);
+    more = true;
+  }
+  // one bounded loop: each round completes at least one event of every live
+  // item, and an item has at most 2 kRedChunk1 events
+  while (__syncthreads_or(more)) {
+    AffRedRound<C> rd{&a};
+    rd.more = false;
+    batch_round<F, BLOCK>(rd, begin, end, a.M, sm);
+    more = rd.more;
+  }
+  for (int k = 0; k < kRedLog1; ++k) {
+    AffDblRound<C> rd{&a};
+    batch_round<F, BLOCK>(rd, begin, end, a.M, sm);
+  }
+  for (uint64_t t = begin + threadIdx.x; t < end; t += BLOCK) {
+    uint32_t x[N], y[N];
+    Jac<F> P;
+    a.R.load(t, x, y);
+    jac_from_affine<C>(P, x, y);
+    a.out_R[t] = P;
+    a.S.load(t, x, y);
+    jac_from_affine<C>(P, x, y);
+    a.out_S[t] = P;
+  }
+}
+
+// One later level for every window row of a set of groups.  Segment k covers
+// threads [t0, t0 + rows * chunks); its input rows have `elems` elements at
+// JR/JS + in_off, its outputs go to + out_off.
+struct LevelSeg {
+  uint64_t t0;
+  uint64_t rows;
+  uint32_t elems;
+  uint32_t chunks;
+  uint64_t in_off;
+  uint64_t out_off;
+};
+
+ECC_DEV uint32_t find_seg(const LevelSeg* s, uint32_t num, uint64_t t) {
+  uint32_t lo = 0, hi = num - 1;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) >> 1;
+    if (s[mid].t0 <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <class C>
+__global__ void k_msm_reduce_level(const LevelSeg* segs, uint32_t n_segs, uint64_t threads,
+                                   Jac<typename C::Fp>* JR, Jac<typename C::Fp>* JS) {
+  using F = typename C::Fp;
   const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  if (t >= (uint64_t)a.n_inst * a.W * chunks) return;
-  const uint32_t u = (uint32_t)(t % chunks);
-  const uint32_t w = (uint32_t)((t / chunks) % a.W);
-  const uint32_t ii = (uint32_t)(t / chunks / a.W);
-  const MsmInst in = a.inst[a.inst_ids[ii]];
-  const uint32_t lo = u * a.chunk;
-  const uint32_t hi = lo + a.chunk < a.elems ? lo + a.chunk : a.elems;  // exclusive
-  const uint64_t win = (uint64_t)ii * a.W + w;                           // window row
+  if (t >= threads) return;
+  const LevelSeg sg = segs[find_seg(segs, n_segs, t)];
+  const uint64_t local = t - sg.t0;
+  const uint64_t row = local / sg.chunks;
+  const uint32_t v = (uint32_t)(local % sg.chunks);
+  const uint32_t lo = v * kRedChunkN;
+  const uint32_t hi = lo + kRedChunkN < sg.elems ? lo + kRedChunkN : sg.elems;  // exclusive
+  const Jac<F>* inR = JR + sg.in_off + row * sg.elems;
+  const Jac<F>* inS = JS + sg.in_off + row * sg.elems;
   Jac<F> Rr, U, Ssum, E;
   jac_set_inf<C>(Rr);
   jac_set_inf<C>(U);
   jac_set_inf<C>(Ssum);
   for (uint32_t e = hi; e-- > lo;) {
-    Jac<F> Se;
-    if (level1) {
-      bucket_sum<C>(a, in.bucket_base + w * (1u << (in.c - 1)) + e, E);
-      Se = E;
-    } else {
-      E = a.in_R[win * a.elems + e];
-      Se = a.in_S[win * a.elems + e];
-    }
-    jac_add<C>(Ssum, Ssum, Se);
-    if (e > lo) {
-      jac_add<C>(Rr, Rr, E);
-      jac_add<C>(U, U, Rr);
-    } else {
-      jac_add<C>(Rr, Rr, E);
-    }
+    E = inS[e];
+    jac_add<C>(Ssum, Ssum, E);
+    E = inR[e];
+    jac_add<C>(Rr, Rr, E);
+    if (e > lo) jac_add<C>(U, U, Rr);
   }
-  for (uint32_t s = 0; s < a.log_span; ++s) jac_dbl<C>(U, U);
   jac_add<C>(Ssum, Ssum, U);
-  a.out_R[win * chunks + u] = Rr;
-  a.out_S[win * chunks + u] = Ssum;
+  if (sg.chunks > 1) {
+    for (int k = 0; k < kRedLogN; ++k) jac_dbl<C>(Rr, Rr);
+  }
+  JR[sg.out_off + row * sg.chunks + v] = Rr;
+  JS[sg.out_off + row * sg.chunks + v] = Ssum;
 }
 
-// result_i = sum_w 2^(c w) S_w (Horner), converted to canonical affine limbs.
+// result_i = sum_w 2^(c w) S_w (Horner), converted to canonical affine limbs;
+// instance i's window sums are S[fin[i] + w].
 template <class C>
-__global__ void k_msm_combine(const MsmInst* inst, const uint32_t* inst_ids, uint32_t n_inst,
-                              uint32_t W, const Jac<typename C::Fp>* S, uint32_t* out_all) {
+__global__ void k_msm_combine(const MsmInst* inst, const uint64_t* fin, uint32_t num,
+                              const Jac<typename C::Fp>* S, uint32_t* out_all) {
   using F = typename C::Fp;
   constexpr int N = F::N;
-  const uint32_t ii = blockIdx.x * blockDim.x + threadIdx.x;
-  if (ii >= n_inst) return;
-  const uint32_t id = inst_ids[ii];
-  const uint32_t c = inst[id].c;
-  Jac<F> acc = S[(uint64_t)ii * W + (W - 1)];
+  const uint32_t id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= num) return;
+  const uint32_t c = inst[id].c, W = inst[id].W;
+  const Jac<F>* Sw = S + fin[id];
+  Jac<F> acc = Sw[W - 1];
   for (int w = (int)W - 2; w >= 0; --w) {
     for (uint32_t s = 0; s < c; ++s) jac_dbl<C>(acc, acc);
-    jac_add<C>(acc, acc, S[(uint64_t)ii * W + w]);
+    jac_add<C>(acc, acc, Sw[w]);
   }
   uint32_t x[N], y[N];
   jac_to_affine<C>(x, y, acc);

@@ -18,7 +18,6 @@ namespace ecc {
 namespace msm_detail {
 
 constexpr int kAccBlock = kGasThreads;
-constexpr uint32_t kReduceChunk = 32;
 
 inline int scalar_bits(int curve) {
   switch (curve) {
@@ -50,7 +49,8 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
   const uint64_t sz_b1 = up((B + 1) * 4);
   const uint64_t sz_kv = up(kAccChunk * NC * 4);
   const uint64_t sz_S = soa_bytes<F>(NC), sz_P = soa_bytes<F>(n_part);
-  const uint64_t bytes = sz_inst + 5 * sz_b1 + 2 * sz_kv + 3 * sz_S + 2 * sz_P + 256;
+  const uint64_t sz_sb = up(n_part * 4);
+  const uint64_t bytes = sz_inst + 5 * sz_b1 + 2 * sz_kv + 3 * sz_S + 3 * sz_P + sz_sb + 256;
   Scratch ws;
   cudaError_t e = ws.alloc(bytes, st);
   if (e != cudaSuccess) return e;
@@ -65,7 +65,8 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
   uint32_t* keys = reinterpret_cast<uint32_t*>(take(sz_kv));
   uint32_t* vals = reinterpret_cast<uint32_t*>(take(sz_kv));
   uint4* sbuf = reinterpret_cast<uint4*>(take(3 * sz_S));
-  uint4* pbuf = reinterpret_cast<uint4*>(take(2 * sz_P));
+  uint4* pbuf = reinterpret_cast<uint4*>(take(3 * sz_P));
+  uint32_t* slot_bucket = reinterpret_cast<uint32_t*>(take(sz_sb));
   e = upload_words(d_inst, L.inst.data(), num * sizeof(MsmInst), st);
   if (e != cudaSuccess) return e;
   // ---- 1-2: digits, counting sort by bucket id
@@ -94,6 +95,7 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
   a.S = PtSoA<F>{SoA<F>{sbuf, NC}, SoA<F>{sbuf + sz_S / 16, NC}};
   a.M = SoA<F>{sbuf + 2 * sz_S / 16, NC};
   a.partial = PtSoA<F>{SoA<F>{pbuf, n_part}, SoA<F>{pbuf + sz_P / 16, n_part}};
+  a.slot_bucket = slot_bucket;
   uint64_t ctas = (uint64_t)device_sm_count() * kGasCtasPerSm;
   uint64_t per = (NC + ctas - 1) / ctas;
   if (per < 32) per = 32;
@@ -106,59 +108,142 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
   k_msm_accumulate<C, kAccBlock><<<(unsigned)ctas, kAccBlock, smem, st>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  // ---- 4-5: per window width: reduction levels, then the window combination
+  // ---- fold the partial sums of every bucket into its first slot
+  if (B) {
+    FoldArgs<C> f;
+    f.poff = poff;
+    f.n_buckets = (uint32_t)B;
+    f.slot_bucket = slot_bucket;
+    f.partial = a.partial;
+    f.M = SoA<F>{pbuf + 2 * sz_P / 16, n_part};
+    e = cudaFuncSetAttribute(k_msm_fold<C, kAccBlock>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_msm_fold<C, kAccBlock><<<(unsigned)(device_sm_count() * kGasCtasPerSm), kAccBlock, smem, st>>>(f);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  // ---- 4: bucket reduction.  Instances are grouped by window width (same
+  // level structure); the items of every level are laid out group-major so a
+  // level of all groups is one launch.
   std::map<uint32_t, std::vector<uint32_t>> groups;
   for (int i = 0; i < num; ++i) groups[L.inst[i].c].push_back((uint32_t)i);
+  std::vector<std::vector<uint32_t>> elems;  // per group: elements per row, by level
+  std::vector<uint64_t> rows;
   for (auto& g : groups) {
-    const uint32_t c = g.first;
-    const std::vector<uint32_t>& ids = g.second;
-    const uint32_t W = L.inst[ids[0]].W;
-    const uint32_t n_inst = (uint32_t)ids.size();
-    Scratch rs;
-    // level sizes
-    std::vector<uint32_t> elems{1u << (c - 1)};
-    while (elems.back() > 1) elems.push_back((elems.back() + kReduceChunk - 1) / kReduceChunk);
-    uint64_t jac_elems = 0;
-    for (size_t l = 1; l < elems.size(); ++l) jac_elems += 2ull * n_inst * W * elems[l];
-    e = rs.alloc(up(n_inst * 4) + jac_elems * sizeof(Jac<F>) + 256, st);
-    if (e != cudaSuccess) return e;
-    char* q = rs.as<char>();
-    uint32_t* d_ids = reinterpret_cast<uint32_t*>(q);
-    q += up(n_inst * 4);
-    e = upload_words(d_ids, ids.data(), n_inst * 4, st);
-    if (e != cudaSuccess) return e;
-    const Jac<F>* in_R = nullptr;
-    const Jac<F>* in_S = nullptr;
-    uint32_t log_span = 0;
-    for (size_t l = 1; l < elems.size(); ++l) {
-      Jac<F>* oR = reinterpret_cast<Jac<F>*>(q);
-      q += (uint64_t)n_inst * W * elems[l] * sizeof(Jac<F>);
-      Jac<F>* oS = reinterpret_cast<Jac<F>*>(q);
-      q += (uint64_t)n_inst * W * elems[l] * sizeof(Jac<F>);
-      ReduceArgs<C> r;
-      r.inst = d_inst;
-      r.inst_ids = d_ids;
-      r.n_inst = n_inst;
-      r.W = W;
-      r.elems = elems[l - 1];
-      r.chunk = kReduceChunk;
-      r.log_span = log_span;
-      r.poff = poff;
-      r.partial = a.partial;
-      r.in_R = in_R;
-      r.in_S = in_S;
-      r.out_R = oR;
-      r.out_S = oS;
-      const uint64_t threads = (uint64_t)n_inst * W * elems[l];
-      k_msm_reduce<C><<<(unsigned)((threads + 63) / 64), 64, 0, st>>>(r, l == 1 ? 1 : 0);
-      e = cudaGetLastError();
-      if (e != cudaSuccess) return e;
-      in_R = oR;
-      in_S = oS;
-      log_span += 5;  // kReduceChunk = 2^5 elements per chunk
+    std::vector<uint32_t> el{1u << (g.first - 1)};
+    el.push_back((el[0] + kRedChunk1 - 1) / kRedChunk1);
+    while (el.back() > 1) el.push_back((el.back() + kRedChunkN - 1) / kRedChunkN);
+    elems.push_back(el);
+    rows.push_back((uint64_t)g.second.size() * L.inst[g.second[0]].W);
+  }
+  const size_t n_groups = elems.size();
+  size_t levels = 0;
+  for (auto& el : elems) levels = std::max(levels, el.size() - 1);
+  // Jacobian arrays: level 1 of every group, then level 2 of every group, ...
+  std::vector<std::vector<uint64_t>> lvl_off(levels + 1, std::vector<uint64_t>(n_groups, 0));
+  uint64_t jac_total = 0;
+  for (size_t l = 1; l <= levels; ++l) {
+    for (size_t g = 0; g < n_groups; ++g) {
+      lvl_off[l][g] = jac_total;
+      if (l < elems[g].size()) jac_total += rows[g] * elems[g][l];
     }
-    if (elems.size() == 1) return cudaErrorInvalidValue;  // c >= 2 always gives a level
-    k_msm_combine<C><<<(n_inst + 63) / 64, 64, 0, st>>>(d_inst, d_ids, n_inst, W, in_S, out);
+  }
+  const uint64_t items = levels == 0 ? 0 : (levels >= 2 ? lvl_off[2][0] : jac_total);
+  std::vector<RedRange> ranges;
+  std::vector<uint64_t> fin(num, 0);
+  {
+    size_t g = 0;
+    uint64_t t = 0;
+    for (auto& grp : groups) {
+      const size_t last = elems[g].size() - 1;
+      for (size_t ii = 0; ii < grp.second.size(); ++ii) {
+        const uint32_t id = grp.second[ii];
+        ranges.push_back(RedRange{t, id, elems[g][1]});
+        t += (uint64_t)L.inst[id].W * elems[g][1];
+        fin[id] = lvl_off[last][g] + (uint64_t)ii * L.inst[id].W;
+      }
+      ++g;
+    }
+  }
+  std::vector<std::vector<LevelSeg>> segs(levels + 1);
+  std::vector<uint64_t> seg_threads(levels + 1, 0);
+  for (size_t l = 2; l <= levels; ++l) {
+    for (size_t g = 0; g < n_groups; ++g) {
+      if (l >= elems[g].size()) continue;
+      segs[l].push_back(LevelSeg{seg_threads[l], rows[g], elems[g][l - 1], elems[g][l],
+                                 lvl_off[l - 1][g], lvl_off[l][g]});
+      seg_threads[l] += rows[g] * elems[g][l];
+    }
+  }
+  uint64_t seg_words = 0;
+  for (size_t l = 2; l <= levels; ++l) seg_words += up(segs[l].size() * sizeof(LevelSeg));
+  const uint64_t sz_red = up(ranges.size() * sizeof(RedRange)) + up(num * 8ull) + seg_words +
+                          2 * up(jac_total * sizeof(Jac<F>)) + 3 * up(items * 4) +
+                          5 * soa_bytes<F>(std::max<uint64_t>(items, 1)) + 256;
+  Scratch rs;
+  e = rs.alloc(sz_red, st);
+  if (e != cudaSuccess) return e;
+  char* q = rs.as<char>();
+  auto take_r = [&](uint64_t b) { char* r = q; q += up(b); return r; };
+  RedRange* d_ranges = reinterpret_cast<RedRange*>(take_r(ranges.size() * sizeof(RedRange)));
+  uint64_t* d_fin = reinterpret_cast<uint64_t*>(take_r(num * 8ull));
+  std::vector<LevelSeg*> d_segs(levels + 1, nullptr);
+  for (size_t l = 2; l <= levels; ++l) d_segs[l] = reinterpret_cast<LevelSeg*>(take_r(segs[l].size() * sizeof(LevelSeg)));
+  Jac<F>* JR = reinterpret_cast<Jac<F>*>(take_r(jac_total * sizeof(Jac<F>)));
+  Jac<F>* JS = reinterpret_cast<Jac<F>*>(take_r(jac_total * sizeof(Jac<F>)));
+  uint32_t* cur_e = reinterpret_cast<uint32_t*>(take_r(items * 4));
+  uint32_t* cur_a = reinterpret_cast<uint32_t*>(take_r(items * 4));
+  uint32_t* lo_b = reinterpret_cast<uint32_t*>(take_r(items * 4));
+  const uint64_t IT = std::max<uint64_t>(items, 1);
+  uint4* rbuf = reinterpret_cast<uint4*>(take_r(5 * soa_bytes<F>(IT)));
+  e = upload_words(d_ranges, ranges.data(), ranges.size() * sizeof(RedRange), st);
+  if (e != cudaSuccess) return e;
+  e = upload_words(d_fin, fin.data(), num * 8ull, st);
+  if (e != cudaSuccess) return e;
+  for (size_t l = 2; l <= levels; ++l) {
+    e = upload_words(d_segs[l], segs[l].data(), segs[l].size() * sizeof(LevelSeg), st);
+    if (e != cudaSuccess) return e;
+  }
+  if (items) {
+    AffRedArgs<C> r;
+    r.inst = d_inst;
+    r.ranges = d_ranges;
+    r.n_ranges = (uint32_t)ranges.size();
+    r.items = items;
+    r.poff = poff;
+    r.partial = a.partial;
+    const uint64_t ss = soa_bytes<F>(IT) / 16;
+    r.R = PtSoA<F>{SoA<F>{rbuf, IT}, SoA<F>{rbuf + ss, IT}};
+    r.S = PtSoA<F>{SoA<F>{rbuf + 2 * ss, IT}, SoA<F>{rbuf + 3 * ss, IT}};
+    r.M = SoA<F>{rbuf + 4 * ss, IT};
+    r.cur_e = cur_e;
+    r.cur_a = cur_a;
+    r.lo_b = lo_b;
+    r.out_R = JR;
+    r.out_S = JS;
+    uint64_t rctas = (uint64_t)device_sm_count() * kGasCtasPerSm;
+    uint64_t rper = (items + rctas - 1) / rctas;
+    if (rper < 32) rper = 32;
+    rctas = (items + rper - 1) / rper;
+    r.per_cta = rper;
+    e = cudaFuncSetAttribute(k_msm_reduce_affine<C, kAccBlock>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_msm_reduce_affine<C, kAccBlock><<<(unsigned)rctas, kAccBlock, smem, st>>>(r);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  for (size_t l = 2; l <= levels; ++l) {
+    if (!seg_threads[l]) continue;
+    k_msm_reduce_level<C><<<(unsigned)((seg_threads[l] + 63) / 64), 64, 0, st>>>(
+        d_segs[l], (uint32_t)segs[l].size(), seg_threads[l], JR, JS);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  // ---- 5: window combination, every instance in one launch
+  if (num) {
+    k_msm_combine<C><<<(num + 63) / 64, 64, 0, st>>>(d_inst, d_fin, (uint32_t)num, JS, out);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
