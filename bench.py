@@ -41,6 +41,9 @@ def parse():
     ap.add_argument("--n", type=int, default=N_VERIFY, help="triples per rank (default 2^20)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-msm", action="store_true", help="skip the MSM and ragged-MSM lines")
+    ap.add_argument("--no-ragged", action="store_true", help="skip the ragged-MSM line")
+    ap.add_argument("--msm-n", type=int, default=1 << 20, help="BLS12-381 MSM bases (default 2^20)")
+    ap.add_argument("--msm-vectors", type=int, default=16, help="scalar vectors per MSM step")
     return ap.parse_args()
 
 
@@ -137,6 +140,27 @@ def gen_inputs(ecc, synth, torch, n, seed):
     return e, dev(r_h), dev(s_h), pub
 
 
+# DRAM traffic of one k_verify launch over 2^20 P-256 triples (dram__bytes_read.sum +
+# dram__bytes_write.sum, one ncu capture; summary and command in
+# profiles/k_verify_p256_2e20_dram.md), valid only for the kernel sources it was
+# taken on: reported as null once any of them has changed.
+VERIFY_TRAFFIC = {"bytes": 82692282368 + 34925375232, "batch": 1 << 20, "digest": "60fdf905a38a77f8",
+                  "sources": ["verify.cuh", "ec.cuh", "fp.cuh", "inv.cuh", "ptx.cuh", "curves_gen.cuh",
+                              "k_verify.cu"]}
+
+
+def verify_traffic(n):
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in VERIFY_TRAFFIC["sources"]:
+        with open(os.path.join(ROOT, "paper_2501_03245_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest()[:16] != VERIFY_TRAFFIC["digest"] or n != VERIFY_TRAFFIC["batch"]:
+        return None
+    return VERIFY_TRAFFIC["bytes"]
+
+
 def imad_peak(ecc, torch, sms):
     """Measured wide multiply-add rate (pairs/s) of the integer pipe."""
     threads = sms * 2048
@@ -184,11 +208,14 @@ def _event_time(torch, fn, reps):
     return a.elapsed_time(b) / 1e3 / reps
 
 
-def bench_msm(ecc, costmodel, synth, torch, peak, rank):
-    """BLS12-381 MSM: 2^20 resident bases a_i G, 16 scalar vectors per step
-    (one ecc_msm_bases call), against the plain form (one MSM launch sequence
-    per vector)."""
-    n, V, curve = 1 << 20, 16, ecc.ECC_BLS12_381
+def bench_msm(ecc, costmodel, synth, torch, peak, rank, n=1 << 20, V=16):
+    """BLS12-381 MSM: n resident bases a_i G (2^20 by default), V scalar vectors
+    per step (16 by default; one ecc_msm_bases call), against the plain form (one
+    MSM launch sequence per vector).  The window width is tuned first."""
+    from paper_2501_03245_gb300 import autotune
+
+    curve = ecc.ECC_BLS12_381
+    tuned = autotune.tune(curve, [n.bit_length() - 1], torch)  # measured window width for n's class
     seed = synth.SEED_BASE + 2 + 1000 * rank
     a, ks = synth.msm_raw(seed, n, BLS_R, V)
     pts = torch.empty((n, 24), dtype=torch.int32, device="cuda")
@@ -207,8 +234,10 @@ def bench_msm(ecc, costmodel, synth, torch, peak, rank):
     c = ecc.ecc_msm_window(curve, n)
     W = -(-256 // c)
     alg = costmodel.msm_modmul(n, W, c) * V * costmodel.imad_per_modmul(12)
-    return {"workload": "MSM BLS12-381 G1, 2^20 resident bases, 16 scalar vectors per step",
+    return {"workload": f"MSM BLS12-381 G1, 2^{n.bit_length() - 1} resident bases, {V} scalar vectors per step"
+                        if n & (n - 1) == 0 else f"MSM BLS12-381 G1, {n} resident bases, {V} scalar vectors per step",
             "value": n * V / t, "unit": "points/s", "ms_per_step": t * 1e3, "window_c": c,
+            "autotuned": {str(k): v for k, v in tuned.items()},
             "plain": {"value": n * V / t1, "unit": "points/s",
                       "form": "one MSM launch sequence per scalar vector"},
             "roofline": {"bound": "alu", "achieved": alg / t / 1e12, "peak": peak / 1e12,
@@ -221,7 +250,10 @@ def bench_ragged(ecc, synth, torch, rank):
     """BN254 ragged batch: 256 MSMs with log-uniform sizes 2^10..2^18, all in one
     launch sequence captured once in a CUDA graph and replayed, against one
     launch sequence per MSM."""
+    from paper_2501_03245_gb300 import autotune
+
     curve = ecc.ECC_BN254
+    tuned = autotune.tune(curve, list(range(10, 19)), torch)  # one window width per size class
     seed = synth.SEED_BASE + 3 + 1000 * rank
     sizes = synth.ragged_sizes(seed, 256)
     total = int(sizes.sum())
@@ -257,6 +289,7 @@ def bench_ragged(ecc, synth, torch, rank):
             "points": total, "value": total / best, "unit": "points/s",
             "graph_replay_ms": graph * 1e3 if graph else None, "eager_ms": eager * 1e3,
             "graph_bit_equal": graph_ok,
+            "autotuned": {str(k): v for k, v in sorted(tuned.items())},
             "plain": {"value": total / per, "unit": "points/s", "form": "one launch sequence per MSM"}}
 
 
@@ -405,7 +438,7 @@ def run_ours(args):
                    "per-item state ~0.8 GiB per step)", "valid_signatures": n_valid},
         "roofline": {"bound": "alu", "kernel": "k_verify<P256>", "achieved": achieved / 1e12,
                      "peak": peak / 1e12, "unit": "T IMAD.WIDE/s", "frac": achieved / peak,
-                     "traffic": None,
+                     "traffic": verify_traffic(n), "traffic_unit": "DRAM bytes per launch",
                      "basis": f"{costmodel.verify_modmul()} modmul x 136 wide mul-adds per verify; "
                               "peak = measured mad.lo/madc.hi pair rate (ecc_bench_imad, same run)"},
         "plain": {"value": plain, "unit": "verifies/s", "form": "one verification per launch"},
@@ -416,8 +449,9 @@ def run_ours(args):
     }
     del e, r, s, pub, ok, e_h, r_h, s_h, p_h, ok_h
     if not args.no_msm:
-        line["msm"] = bench_msm(ecc, costmodel, synth, torch, peak, rank)
-        line["ragged"] = bench_ragged(ecc, synth, torch, rank)
+        line["msm"] = bench_msm(ecc, costmodel, synth, torch, peak, rank, args.msm_n, args.msm_vectors)
+        if not args.no_ragged:
+            line["ragged"] = bench_ragged(ecc, synth, torch, rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline
     if rank == 0:

@@ -98,21 +98,20 @@ enum AddKind : int { ADD_REGULAR = 0, ADD_DOUBLE = 1, ADD_RET_T = 2, ADD_RET_P =
 // Denominator of lambda for P + T (Eqn 2, or PDBL when P = T), or 1 when the
 // result needs no slope (an operand is O, or P = -T).
 template <class C>
+ECC_DEV int add_kind(const uint32_t* xp, const uint32_t* yp, const uint32_t* xt, const uint32_t* yt) {
+  using F = typename C::Fp;
+  if (pt_is_inf<F>(xp, yp)) return ADD_RET_T;
+  if (pt_is_inf<F>(xt, yt)) return ADD_RET_P;
+  if (!fe_eq<F>(xp, xt)) return ADD_REGULAR;
+  if (fe_eq<F>(yp, yt) && !fe_is_zero<F>(yp)) return ADD_DOUBLE;
+  return ADD_RET_INF;
+}
+
+template <class C>
 ECC_DEV int add_den(uint32_t* den, const uint32_t* xp, const uint32_t* yp, const uint32_t* xt,
                     const uint32_t* yt) {
   using F = typename C::Fp;
-  int kind;
-  if (pt_is_inf<F>(xp, yp)) {
-    kind = ADD_RET_T;
-  } else if (pt_is_inf<F>(xt, yt)) {
-    kind = ADD_RET_P;
-  } else if (!fe_eq<F>(xp, xt)) {
-    kind = ADD_REGULAR;
-  } else if (fe_eq<F>(yp, yt) && !fe_is_zero<F>(yp)) {
-    kind = ADD_DOUBLE;
-  } else {
-    kind = ADD_RET_INF;
-  }
+  const int kind = add_kind<C>(xp, yp, xt, yt);
   if (kind == ADD_REGULAR) {
     fe_sub<F>(den, xt, xp);
   } else if (kind == ADD_DOUBLE) {

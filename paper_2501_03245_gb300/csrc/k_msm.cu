@@ -28,13 +28,14 @@ std::mutex g_win_mu;
 std::map<std::pair<int, int>, int> g_window_table;  // (curve, floor(log2 n)) -> c
 
 // Cost model: one batched addition (6 modmul) per (point, window) digit plus the
-// Jacobian bucket reduction (about three additions of ~15 modmul per bucket).
+// bucket reduction, about two and a half batched additions per bucket (the walk's
+// A and S events and the fold's share).
 int model_window(int curve, uint64_t n) {
   int best = 4;
   double best_cost = 1e300;
   for (int c = 4; c <= 20; ++c) {
     const double W = msm_detail::windows_for(curve, c);
-    const double cost = (double)n * W * 6.0 + W * (double)(1u << (c - 1)) * 45.0;
+    const double cost = (double)n * W * 6.0 + W * (double)(1u << (c - 1)) * 15.0;
     if (cost < best_cost) {
       best_cost = cost;
       best = c;

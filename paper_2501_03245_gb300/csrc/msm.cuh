@@ -27,7 +27,6 @@
 namespace ecc {
 
 constexpr int kAccChunk = 32;       // entries per running-sum chunk (rounds of step 3)
-constexpr uint32_t kNoKey = 0xffffffffu;
 
 struct MsmInst {
   uint32_t n;            // points of the instance
@@ -112,10 +111,11 @@ __global__ void k_msm_count(const MsmInst* inst, int num, const uint32_t* __rest
   });
 }
 
-// Entries are written chunk-transposed: entry p goes to [p % CH][p / CH].
+// Entries are written chunk-transposed: entry p goes to [p % CH][p / CH].  Only
+// the point index is stored; the bucket of position p follows from the offsets.
 template <class C>
 __global__ void k_msm_scatter(const MsmInst* inst, int num, const uint32_t* __restrict__ scalars,
-                              uint64_t total, uint32_t* __restrict__ cursor, uint32_t* __restrict__ keys,
+                              uint64_t total, uint32_t* __restrict__ cursor,
                               uint32_t* __restrict__ vals, uint64_t n_chunks) {
   const uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (g >= total) return;
@@ -129,9 +129,7 @@ __global__ void k_msm_scatter(const MsmInst* inst, int num, const uint32_t* __re
   for_each_digit(k, in.c, in.W, [&](int w, int d) {
     const uint32_t b = in.bucket_base + w * half + (uint32_t)(d < 0 ? -d : d) - 1;
     const uint32_t p = atomicAdd(cursor + b, 1u);
-    const uint64_t slot = (uint64_t)(p % kAccChunk) * n_chunks + p / kAccChunk;
-    keys[slot] = b;
-    vals[slot] = pidx | (d < 0 ? 0x80000000u : 0u);
+    vals[(uint64_t)(p % kAccChunk) * n_chunks + p / kAccChunk] = pidx | (d < 0 ? 0x80000000u : 0u);
   });
 }
 
@@ -149,17 +147,17 @@ static __global__ void k_msm_npart(const uint32_t* __restrict__ off, uint32_t n_
 template <class C>
 struct AccArgs {
   using F = typename C::Fp;
-  const uint32_t* keys;   // [CH][n_chunks]
-  const uint32_t* vals;
+  const uint32_t* vals;   // sorted (point index | sign bit), [CH][n_chunks]
   const uint32_t* off;    // bucket offsets (exclusive scan), off[n_buckets] = entries
   const uint32_t* poff;   // partial-slot offsets per bucket
   uint32_t n_buckets;
   uint64_t n_chunks;
   const uint32_t* bases;  // AoS Montgomery affine points, 2N words each
+  uint32_t* cur;          // bucket of the chunk's current entry
   PtSoA<F> S;             // running sum per chunk
   PtSoA<F> partial;       // partial bucket sums
-  uint32_t* slot_bucket;  // bucket of every partial slot
-  SoA<F> M;
+  SoA<F> M;               // GAS prefix products
+  SoA<F> D;               // this round's denominators
   uint64_t per_cta;
 };
 
@@ -186,6 +184,17 @@ ECC_DEV uint64_t partial_slot(const AccArgs<C>& a, uint32_t b, uint64_t chunk) {
   return a.poff[b] + (chunk - a.off[b] / kAccChunk);
 }
 
+// The bucket holding sorted position p: the last b in [lo, n) with off[b] <= p
+// (requires off[lo] <= p < off[n]).
+ECC_DEV uint32_t bucket_of(const uint32_t* off, uint32_t lo, uint32_t n, uint32_t p) {
+  uint32_t hi = n;
+  while (hi - lo > 1) {
+    const uint32_t mid = lo + ((hi - lo) >> 1);
+    if (off[mid] <= p) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
 template <class C>
 struct AccRound {
   using F = typename C::Fp;
@@ -194,49 +203,59 @@ struct AccRound {
   const AccArgs<C>* a;
   int j;
   uint32_t entries;
-  int kind;
+  uint32_t bucket, prev;
   bool start, live;
-  ECC_DEV void classify(size_t c, uint32_t& key, uint32_t& val, uint32_t& prev) {
-    const uint64_t p = (uint64_t)c * kAccChunk + j;
+  // Entry j of chunk c: its bucket, and whether it starts a new running sum.
+  ECC_DEV void classify(size_t c) {
+    const uint32_t p = (uint32_t)(c * kAccChunk + j);
     live = p < entries;
-    key = live ? a->keys[(uint64_t)j * a->n_chunks + c] : kNoKey;
-    val = live ? a->vals[(uint64_t)j * a->n_chunks + c] : 0u;
-    prev = (live && j > 0) ? a->keys[(uint64_t)(j - 1) * a->n_chunks + c] : kNoKey;
-    start = live && (j == 0 || key != prev);
-  }
-  ECC_DEV void den_c(size_t c, int, uint32_t* d) {
-    uint32_t key, val, prev;
-    classify(c, key, val, prev);
-    if (!live || start) {
-      fe_set_one<F>(d);
-      kind = ADD_RET_T;
+    if (!live) return;
+    if (j == 0) {
+      bucket = bucket_of(a->off, 0, a->n_buckets, p);
+      start = true;
       return;
     }
-    uint32_t xs[N], ys[N], xp[N], yp[N];
-    a->S.load(c, xs, ys);
-    load_base<C>(*a, val, xp, yp);
-    kind = add_den<C>(d, xs, ys, xp, yp);
+    prev = a->cur[c];
+    if (p < a->off[prev + 1]) {
+      bucket = prev;
+      start = false;
+      return;
+    }
+    start = true;
+    bucket = prev + 1;  // usually the next bucket; skip empty ones otherwise
+    if (a->off[bucket + 1] <= p) bucket = bucket_of(a->off, bucket + 1, a->n_buckets, p);
   }
-  ECC_DEV void den_d(size_t c, int k, uint32_t* d) { den_c(c, k, d); }
+  ECC_DEV void den_c(size_t c, int, uint32_t* d) {
+    classify(c);
+    if (!live || start) {
+      fe_set_one<F>(d);
+    } else {
+      uint32_t xs[N], ys[N], xp[N], yp[N];
+      a->S.load(c, xs, ys);
+      load_base<C>(*a, a->vals[(uint64_t)j * a->n_chunks + c], xp, yp);
+      add_den<C>(d, xs, ys, xp, yp);
+    }
+    a->D.store(c, d);
+  }
+  ECC_DEV void den_d(size_t c, int, uint32_t* d) { a->D.load(c, d); }
   ECC_DEV void finish(size_t c, const uint32_t (*inv)[N]) {
+    classify(c);
     if (!live) return;
-    uint32_t key, val, prev;
-    classify(c, key, val, prev);
     uint32_t xs[N], ys[N], xp[N], yp[N];
-    load_base<C>(*a, val, xp, yp);
+    load_base<C>(*a, a->vals[(uint64_t)j * a->n_chunks + c], xp, yp);
     if (start) {
       if (j > 0) {
         a->S.load(c, xs, ys);
-        const uint64_t ps = partial_slot(*a, prev, c);
-        a->partial.store(ps, xs, ys);
-        a->slot_bucket[ps] = prev;
+        a->partial.store(partial_slot(*a, prev, c), xs, ys);
       }
       a->S.store(c, xp, yp);
     } else {
       a->S.load(c, xs, ys);
+      const int kind = add_kind<C>(xs, ys, xp, yp);
       add_finish<C>(xs, ys, kind, inv[0], xs, ys, xp, yp);
       a->S.store(c, xs, ys);
     }
+    if (start) a->cur[c] = bucket;
   }
 };
 
@@ -257,15 +276,9 @@ __global__ void __launch_bounds__(BLOCK, kGasResidentThreads / BLOCK) k_msm_accu
   }
   // flush the last running sum of every chunk
   for (uint64_t c = begin + threadIdx.x; c < end; c += BLOCK) {
-    const uint64_t last = c * kAccChunk + kAccChunk - 1 < entries ? c * kAccChunk + kAccChunk - 1
-                                                                  : entries - 1;
-    const int jl = (int)(last - c * kAccChunk);
-    const uint32_t key = a.keys[(uint64_t)jl * a.n_chunks + c];
     uint32_t xs[N], ys[N];
     a.S.load(c, xs, ys);
-    const uint64_t ps = partial_slot(a, key, c);
-    a.partial.store(ps, xs, ys);
-    a.slot_bucket[ps] = key;
+    a.partial.store(partial_slot(a, a.cur[c], c), xs, ys);
   }
 }
 
@@ -313,7 +326,6 @@ struct FoldArgs {
   using F = typename C::Fp;
   const uint32_t* poff;         // partial-slot offsets per bucket (n_buckets + 1)
   uint32_t n_buckets;
-  const uint32_t* slot_bucket;  // bucket of every partial slot
   PtSoA<F> partial;
   SoA<F> M;                     // GAS prefix products, one per slot
 };
@@ -328,19 +340,14 @@ ECC_DEV uint32_t lower_bound_u32(const uint32_t* v, uint32_t n, uint64_t x) {
   return lo;
 }
 
-// Round with stride h: slot l of a bucket with k partials adds slot l + h when
-// l is a multiple of 2h and l + h < k.
+// Round with stride h: slot l of a bucket with k partials adds slot l + h for
+// every l that is a multiple of 2h with l + h < k.
 template <class C>
 struct FoldOp {
   using F = typename C::Fp;
   static constexpr int N = F::N;
   const FoldArgs<C>* a;
   uint32_t h;
-  ECC_DEV bool active(uint64_t s) const {
-    const uint32_t b = a->slot_bucket[s];
-    const uint32_t l = (uint32_t)(s - a->poff[b]), k = a->poff[b + 1] - a->poff[b];
-    return (l & (2 * h - 1)) == 0 && l + h < k;
-  }
   ECC_DEV int den(uint64_t s, uint32_t* d) const {
     uint32_t x0[N], y0[N], x1[N], y1[N];
     a->partial.load(s, x0, y0);
@@ -356,6 +363,9 @@ struct FoldOp {
   }
 };
 
+// Items are buckets: in each round a thread performs all pair additions of its
+// buckets (one for a bucket of two or three partials), so lanes stay converged
+// unless a bucket holds many partials.
 template <class C, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, kGasResidentThreads / BLOCK) k_msm_fold(FoldArgs<C> a) {
   using F = typename C::Fp;
@@ -369,10 +379,8 @@ __global__ void __launch_bounds__(BLOCK, kGasResidentThreads / BLOCK) k_msm_fold
   const uint32_t b1 = blockIdx.x + 1 == gridDim.x
                           ? a.n_buckets
                           : lower_bound_u32(a.poff, a.n_buckets, (blockIdx.x + 1) * share);
-  const uint64_t s0 = a.poff[b0], s1 = b1 > b0 ? a.poff[b1] : s0;
   uint32_t kmax = 0;
-  for (uint64_t s = s0 + threadIdx.x; s < s1; s += BLOCK) {
-    const uint32_t b = a.slot_bucket[s];
+  for (uint32_t b = b0 + threadIdx.x; b < b1; b += BLOCK) {
     const uint32_t k = a.poff[b + 1] - a.poff[b];
     kmax = k > kmax ? k : kmax;
   }
@@ -381,27 +389,35 @@ __global__ void __launch_bounds__(BLOCK, kGasResidentThreads / BLOCK) k_msm_fold
     FoldOp<C> op{&a, h};
     uint32_t run[N];
     fe_set_one<F>(run);
-    for (uint64_t s = s0 + threadIdx.x; s < s1; s += BLOCK) {
-      if (!op.active(s)) continue;
-      uint32_t d[N];
-      a.M.store(s, run);
-      op.den(s, d);
-      mont_mul<F>(run, run, d);
+    for (uint32_t b = b0 + threadIdx.x; b < b1; b += BLOCK) {
+      const uint64_t p = a.poff[b];
+      const uint32_t k = (uint32_t)(a.poff[b + 1] - p);
+      for (uint32_t l = 0; l + h < k; l += 2 * h) {
+        uint32_t d[N];
+        a.M.store(p + l, run);
+        op.den(p + l, d);
+        mont_mul<F>(run, run, d);
+      }
     }
     uint32_t inv[N];
     cta_invert<F, BLOCK>(inv, run, sm);
-    if (s0 + threadIdx.x < s1) {
-      const uint64_t first = s0 + threadIdx.x;
-      const uint64_t last = first + ((s1 - 1 - first) / BLOCK) * BLOCK;
-      for (uint64_t s = last + BLOCK; s > first;) {
-        s -= BLOCK;
-        if (!op.active(s)) continue;
-        uint32_t d[N], pre[N], mine[N];
-        const int kind = op.den(s, d);
-        a.M.load(s, pre);
-        mont_mul<F>(mine, inv, pre);
-        mont_mul<F>(inv, inv, d);
-        op.finish(s, kind, mine);
+    if (b0 + threadIdx.x < b1) {
+      const uint32_t first = b0 + threadIdx.x;
+      const uint32_t last = first + ((b1 - 1 - first) / BLOCK) * BLOCK;
+      for (uint32_t b = last + BLOCK; b > first;) {
+        b -= BLOCK;
+        const uint64_t p = a.poff[b];
+        const uint32_t k = (uint32_t)(a.poff[b + 1] - p);
+        if (k <= h) continue;
+        for (uint32_t l = ((k - h - 1) / (2 * h)) * (2 * h);; l -= 2 * h) {
+          uint32_t d[N], pre[N], mine[N];
+          const int kind = op.den(p + l, d);
+          a.M.load(p + l, pre);
+          mont_mul<F>(mine, inv, pre);
+          mont_mul<F>(inv, inv, d);
+          op.finish(p + l, kind, mine);
+          if (l == 0) break;
+        }
       }
     }
   }

@@ -47,10 +47,9 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
   auto up = [](uint64_t b) { return (b + 255) / 256 * 256; };
   const uint64_t sz_inst = up(num * sizeof(MsmInst));
   const uint64_t sz_b1 = up((B + 1) * 4);
-  const uint64_t sz_kv = up(kAccChunk * NC * 4);
+  const uint64_t sz_kv = up(kAccChunk * NC * 4), sz_cur = up(NC * 4);
   const uint64_t sz_S = soa_bytes<F>(NC), sz_P = soa_bytes<F>(n_part);
-  const uint64_t sz_sb = up(n_part * 4);
-  const uint64_t bytes = sz_inst + 5 * sz_b1 + 2 * sz_kv + 3 * sz_S + 3 * sz_P + sz_sb + 256;
+  const uint64_t bytes = sz_inst + 5 * sz_b1 + sz_kv + sz_cur + 4 * sz_S + 3 * sz_P + 256;
   Scratch ws;
   cudaError_t e = ws.alloc(bytes, st);
   if (e != cudaSuccess) return e;
@@ -62,11 +61,10 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
   uint32_t* cursor = reinterpret_cast<uint32_t*>(take(sz_b1));
   uint32_t* npart = reinterpret_cast<uint32_t*>(take(sz_b1));
   uint32_t* poff = reinterpret_cast<uint32_t*>(take(sz_b1));
-  uint32_t* keys = reinterpret_cast<uint32_t*>(take(sz_kv));
   uint32_t* vals = reinterpret_cast<uint32_t*>(take(sz_kv));
-  uint4* sbuf = reinterpret_cast<uint4*>(take(3 * sz_S));
+  uint32_t* cur = reinterpret_cast<uint32_t*>(take(sz_cur));
+  uint4* sbuf = reinterpret_cast<uint4*>(take(4 * sz_S));
   uint4* pbuf = reinterpret_cast<uint4*>(take(3 * sz_P));
-  uint32_t* slot_bucket = reinterpret_cast<uint32_t*>(take(sz_sb));
   e = upload_words(d_inst, L.inst.data(), num * sizeof(MsmInst), st);
   if (e != cudaSuccess) return e;
   // ---- 1-2: digits, counting sort by bucket id
@@ -82,11 +80,11 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
   e = exclusive_scan(npart, B, poff, st);
   if (e != cudaSuccess) return e;
   if (L.total_points)
-    k_msm_scatter<C><<<pb, 256, 0, st>>>(d_inst, num, scalars, L.total_points, cursor, keys, vals, NC);
+    k_msm_scatter<C><<<pb, 256, 0, st>>>(d_inst, num, scalars, L.total_points, cursor, vals, NC);
   // ---- 3: bucket accumulation (batched affine, one launch)
   AccArgs<C> a;
-  a.keys = keys;
   a.vals = vals;
+  a.cur = cur;
   a.off = off;
   a.poff = poff;
   a.n_buckets = (uint32_t)B;
@@ -94,8 +92,8 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
   a.bases = bases_mont;
   a.S = PtSoA<F>{SoA<F>{sbuf, NC}, SoA<F>{sbuf + sz_S / 16, NC}};
   a.M = SoA<F>{sbuf + 2 * sz_S / 16, NC};
+  a.D = SoA<F>{sbuf + 3 * sz_S / 16, NC};
   a.partial = PtSoA<F>{SoA<F>{pbuf, n_part}, SoA<F>{pbuf + sz_P / 16, n_part}};
-  a.slot_bucket = slot_bucket;
   uint64_t ctas = (uint64_t)device_sm_count() * kGasCtasPerSm;
   uint64_t per = (NC + ctas - 1) / ctas;
   if (per < 32) per = 32;
@@ -113,7 +111,6 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
     FoldArgs<C> f;
     f.poff = poff;
     f.n_buckets = (uint32_t)B;
-    f.slot_bucket = slot_bucket;
     f.partial = a.partial;
     f.M = SoA<F>{pbuf + 2 * sz_P / 16, n_part};
     e = cudaFuncSetAttribute(k_msm_fold<C, kAccBlock>,
