@@ -76,7 +76,9 @@ int ecc_limbs(ecc_curve_t curve);
  * multiplication; inputs are converted into Montgomery form and back).
  * field: ECC_FIELD_BASE (q = p) or ECC_FIELD_SCALAR (q = group order n).
  * a, b, out: n rows of L limbs (L = ecc_limbs() for the base field, 8 for the
- * scalar field); inputs must be canonical. */
+ * scalar field); inputs must be canonical.  On the P-256 base field these
+ * unit operations reduce with the special form of the prime (Section 4.2); the
+ * results are the same integers. */
 int ecc_fp_mul(ecc_curve_t curve, int field, size_t n, const uint32_t* a, const uint32_t* b,
                uint32_t* out, void* stream);
 
@@ -214,8 +216,13 @@ int ecc_msm_set_window(ecc_curve_t curve, int log2_n, int c);
 int ecc_bench_imad(size_t threads, int iters, uint32_t* sink, void* stream);
 
 /* Montgomery multiplications in registers: each thread runs `iters` rounds of
- * 4 independent mont_mul chains of the curve's base field.  sink as above. */
-int ecc_bench_modmul(ecc_curve_t curve, size_t threads, int iters, uint32_t* sink, void* stream);
+ * 4 independent mont_mul chains of the curve's base field.  reduction 0 = the
+ * generic Montgomery reduction (Algorithm 2, as in every fused kernel);
+ * 1 = the special-form reduction of Section 4.2 (P-256 only, ECC_EUNSUPPORTED
+ * otherwise; the ecc_fp_* unit operations on the P-256 base field use it).
+ * sink as above. */
+int ecc_bench_modmul(ecc_curve_t curve, int reduction, size_t threads, int iters, uint32_t* sink,
+                     void* stream);
 
 /* Inversion latency probe: each thread runs a chain of `iters` dependent
  * inversions in the curve's base field, method 0 = Fermat (Section 2.2),

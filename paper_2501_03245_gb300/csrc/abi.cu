@@ -449,10 +449,15 @@ int ecc_bench_imad(size_t threads, int iters, uint32_t* sink, void* stream) {
   return ok();
 }
 
-int ecc_bench_modmul(ecc_curve_t curve, size_t threads, int iters, uint32_t* sink, void* stream) {
+int ecc_bench_modmul(ecc_curve_t curve, int reduction, size_t threads, int iters, uint32_t* sink,
+                     void* stream) {
   if (!valid_curve(curve)) return fail(ECC_EINVAL, "ecc_bench_modmul: unknown curve");
-  if (threads == 0 || iters < 0 || !sink) return fail(ECC_EINVAL, "ecc_bench_modmul: bad argument");
-  cudaError_t e = launch_bench_modmul(curve, threads, iters, sink, static_cast<cudaStream_t>(stream));
+  if (threads == 0 || iters < 0 || !sink || reduction < 0 || reduction > 1)
+    return fail(ECC_EINVAL, "ecc_bench_modmul: bad argument");
+  if (reduction == 1 && curve != ECC_P256)
+    return fail(ECC_EUNSUPPORTED, "ecc_bench_modmul: the special-form reduction is P-256 only");
+  cudaError_t e = launch_bench_modmul(curve, reduction, threads, iters, sink,
+                                      static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "ecc_bench_modmul");
   return ok();
 }

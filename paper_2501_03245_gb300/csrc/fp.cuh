@@ -3,8 +3,8 @@
 // Elements are N little-endian 32-bit limbs (N even: 8 for 254/256-bit fields,
 // 12 for the 381-bit field) held in registers, in Montgomery form a*R mod q with
 // R = 2^(32N), canonical in [0, q).  A field is a traits class F with
-//   N, QINV = -q^-1 mod 2^32, p(i), r2(i) = R^2 mod q, one(i) = R mod q,
-//   pm2(i) = q - 2.
+//   N, QINV = -q^-1 mod 2^32, FORM (0 generic, 1 the P-256 prime), p(i),
+//   r2(i) = R^2 mod q, one(i) = R mod q, pm2(i) = q - 2.
 //
 // mont_mul is Montgomery multiplication (Algorithm 2) with the operand-scanning
 // order interleaved row by row.  Each row A*b_i is split into an "even" chain
@@ -131,6 +131,38 @@ ECC_DEV void fe_neg(uint32_t* r, const uint32_t* a) {
   fe_sub<F>(r, z, a);
 }
 
+// Reduction row of mont_mul for q = 2^256 - 2^224 + 2^192 + 2^96 - 1 (NIST
+// P-256), the special-form reduction of Section 4.2 done our way: -q^-1 mod
+// 2^32 is 1, so u = T_0, and every limb of q is 0, 1 or 2^32 - 1, so
+// u q_j needs no multiplication: u (2^32 - 1) = hu 2^32 + nu with nu = -u mod
+// 2^32 and hu = u - [u != 0].  The even chain adds u (q_0 + q_2 2^64 + q_6 2^192)
+// to c (q_4 = 0): word 0 becomes u + nu, which is 0 with carry [u != 0], and
+// that carry plus hu makes u at word 1.  The odd chain adds
+// u (q_1 + q_7 2^192) to d (q_3 = q_5 = 0).  Both chains are additions: the
+// row costs no multiply-adds instead of 2N + 2.
+ECC_DEV void p256_reduce_row(uint32_t* c, uint32_t* d) {
+  const uint32_t u = c[0];
+  const uint32_t nu = 0u - u;
+  const uint32_t hu = u - (u != 0u ? 1u : 0u);
+  c[1] = ptx::add_cc(c[1], u);
+  c[2] = ptx::addc_cc(c[2], nu);
+  c[3] = ptx::addc_cc(c[3], hu);
+  c[4] = ptx::addc_cc(c[4], 0);
+  c[5] = ptx::addc_cc(c[5], 0);
+  c[6] = ptx::addc_cc(c[6], u);
+  c[7] = ptx::addc_cc(c[7], 0);
+  c[8] = ptx::addc(c[8], 0);
+  d[0] = ptx::add_cc(d[0], nu);
+  d[1] = ptx::addc_cc(d[1], hu);
+  d[2] = ptx::addc_cc(d[2], 0);
+  d[3] = ptx::addc_cc(d[3], 0);
+  d[4] = ptx::addc_cc(d[4], 0);
+  d[5] = ptx::addc_cc(d[5], 0);
+  d[6] = ptx::addc_cc(d[6], nu);
+  d[7] = ptx::addc_cc(d[7], hu);
+  d[8] = ptx::addc(d[8], 0);
+}
+
 // Montgomery product r = a * b * R^-1 mod q (r may alias a or b).
 template <class F>
 ECC_DEV void mont_mul(uint32_t* r, const uint32_t* a, const uint32_t* b) {
@@ -181,6 +213,10 @@ ECC_DEV void mont_mul(uint32_t* r, const uint32_t* a, const uint32_t* b) {
       c[j + 1] = ptx::madc_hi_cc(a[j], bi, c[j + 1]);
     }
     c[N] = ptx::addc(c[N], 0);
+    if constexpr (F::FORM == 1) {
+      p256_reduce_row(c, d);
+      continue;
+    }
     // reduction row: u = T_0 * QINV, T += u * q (even and odd chains)
     const uint32_t u = c[0] * F::QINV;
     c[0] = ptx::mad_lo_cc(u, F::p(0), c[0]);

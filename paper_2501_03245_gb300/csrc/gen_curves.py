@@ -36,6 +36,15 @@ CURVES = [
 ]
 
 
+# Moduli that also get a second traits class with a reduction of their own
+# (fp.cuh, mont_mul): FORM 1 is the NIST P-256 prime 2^256 - 2^224 + 2^192 +
+# 2^96 - 1, whose -q^-1 mod 2^32 is 1 and whose limbs are 0, 1 and 2^32 - 1
+# only.  The main traits classes are FORM 0 (the generic Montgomery reduction).
+SPECIAL = {
+    0xFFFFFFFF00000001000000000000000000000000FFFFFFFFFFFFFFFFFFFFFFFF: ("P256FpSpecial", 1),
+}
+
+
 def limbs(v, n):
     return [(v >> (32 * i)) & 0xFFFFFFFF for i in range(n)]
 
@@ -56,10 +65,14 @@ def field(name, q):
     s += f"  static constexpr int N = {n};\n"
     s += f"  static constexpr int BITS = {q.bit_length()};\n"
     s += f"  static constexpr uint32_t QINV = 0x{qinv:08x}u;\n"
+    s += "  static constexpr int FORM = 0;\n"
     s += f"  static constexpr uint64_t QINV62 = 0x{pow(q, -1, 1 << 62):016x}ull;  // q^-1 mod 2^62\n"
     s += arr("p", q, n) + arr("r2", R * R % q, n) + arr("one", R % q, n) + arr("pm2", q - 2, n)
     s += arr("r3", R * R * R % q, n)
     s += "};\n\n"
+    if q in SPECIAL:
+        sname, form = SPECIAL[q]
+        s += f"struct {sname} : {name} {{\n  static constexpr int FORM = {form};\n}};\n\n"
     return s, n, R
 
 

@@ -83,7 +83,7 @@ cudaError_t launch_msm_bases(void* handle, uint32_t num_vectors, const uint64_t*
 
 // benchmarks
 cudaError_t launch_bench_imad(size_t threads, int iters, uint32_t* sink, cudaStream_t st);
-cudaError_t launch_bench_modmul(int curve, size_t threads, int iters, uint32_t* sink,
+cudaError_t launch_bench_modmul(int curve, int reduction, size_t threads, int iters, uint32_t* sink,
                                 cudaStream_t st);
 cudaError_t launch_bench_inv(int curve, int method, size_t threads, int iters, uint32_t* sink,
                              cudaStream_t st);

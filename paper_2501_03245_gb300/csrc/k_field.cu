@@ -182,7 +182,7 @@ int field_limbs(int curve, int field) {
   switch ((curve) * 2 + (field)) {                      \
     case 0: { using F = Secp256k1Fp; return CALL; }     \
     case 1: { using F = Secp256k1Fn; return CALL; }     \
-    case 2: { using F = P256Fp; return CALL; }          \
+    case 2: { using F = P256FpSpecial; return CALL; }   \
     case 3: { using F = P256Fn; return CALL; }          \
     case 4: { using F = BN254Fp; return CALL; }         \
     case 5: { using F = BN254Fn; return CALL; }         \
@@ -238,9 +238,14 @@ cudaError_t launch_bench_inv(int curve, int method, size_t threads, int iters, u
   return cudaGetLastError();
 }
 
-cudaError_t launch_bench_modmul(int curve, size_t threads, int iters, uint32_t* sink,
-                                cudaStream_t st) {
+cudaError_t launch_bench_modmul(int curve, int reduction, size_t threads, int iters,
+                                uint32_t* sink, cudaStream_t st) {
   const unsigned b = (unsigned)((threads + 255) / 256);
+  if (reduction == 1) {
+    if (curve != 1) return cudaErrorNotSupported;
+    k_bench_modmul<P256FpSpecial><<<b, 256, 0, st>>>(iters, sink);
+    return cudaGetLastError();
+  }
   switch (curve) {
     case 0: k_bench_modmul<Secp256k1Fp><<<b, 256, 0, st>>>(iters, sink); break;
     case 1: k_bench_modmul<P256Fp><<<b, 256, 0, st>>>(iters, sink); break;

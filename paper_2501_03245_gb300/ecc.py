@@ -56,7 +56,7 @@ _SIGS = {
     "ecc_bench_imad": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "ecc_bench_inv": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_size_t, ctypes.c_int,
                                      ctypes.c_void_p, ctypes.c_void_p]),
-    "ecc_bench_modmul": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p,
+    "ecc_bench_modmul": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p,
                                         ctypes.c_void_p]),
 }
 
@@ -233,8 +233,8 @@ def ecc_bench_imad(threads, iters, sink, stream=None):
     return _check(load().ecc_bench_imad(threads, iters, _ptr(sink), _stream(stream)))
 
 
-def ecc_bench_modmul(curve, threads, iters, sink, stream=None):
-    return _check(load().ecc_bench_modmul(curve, threads, iters, _ptr(sink), _stream(stream)))
+def ecc_bench_modmul(curve, reduction, threads, iters, sink, stream=None):
+    return _check(load().ecc_bench_modmul(curve, reduction, threads, iters, _ptr(sink), _stream(stream)))
 
 
 def ecc_bench_inv(curve, method, threads, iters, sink, stream=None):

@@ -88,3 +88,55 @@ def test_argument_errors(gpu_lib):
     with pytest.raises(gpu_lib.EccError) as e:
         gpu_lib.ecc_verify_batch(2, 4, a, a, a, a, a)
     assert e.value.code == gpu_lib.ECC_EUNSUPPORTED
+
+
+def _carry_heavy(q, n, seed):
+    """Operands whose limbs are mostly 0, 1, 2^31 and 2^32 - 1, values next to q
+    and to powers of two: they drive long carry runs and zero Montgomery digits
+    through a reduction that replaces multiply-adds by additions."""
+    rng = random.Random(seed)
+    out = []
+    while len(out) < n:
+        k = rng.randrange(5)
+        if k == 0:
+            v = sum(rng.choice([0, 1, 0x80000000, 0xFFFFFFFF, rng.randrange(1 << 32)]) << (32 * i)
+                    for i in range(8))
+        elif k == 1:
+            v = q - 1 - rng.randrange(1 << rng.randrange(1, 200))
+        elif k == 2:
+            v = 1 << rng.randrange(256)
+        elif k == 3:
+            v = q - (1 << rng.randrange(256))
+        else:
+            v = rng.randrange(1 << rng.randrange(1, 257))
+        out.append(v % q)
+    return out
+
+
+def test_fp_mul_p256_special_form(gpu_lib):
+    """The P-256 base-field unit operations use the special-form reduction of
+    Section 4.2 (u = T_0, u q by additions): every product against the oracle on
+    operands chosen to stress its carries."""
+    import torch
+
+    cid, q = 1, curves.P256.p
+    n = 8192
+    A, B = _carry_heavy(q, n, 11), _carry_heavy(q, n, 12)
+    a, b = to_cuda(synth.ints_to_limbs(A, 8)), to_cuda(synth.ints_to_limbs(B, 8))
+    out = torch.zeros_like(a)
+    gpu_lib.ecc_fp_mul(cid, 0, n, a, b, out)
+    torch.cuda.synchronize()
+    assert synth.limbs_to_ints(from_cuda(out)) == [field.mul(q, x, y) for x, y in zip(A, B)]
+
+
+def test_bench_modmul_reductions(gpu_lib):
+    import torch
+
+    from paper_2501_03245_gb300 import ecc
+
+    sink = torch.zeros(512, dtype=torch.int32, device="cuda")
+    gpu_lib.ecc_bench_modmul(1, 1, 512, 4, sink)
+    gpu_lib.ecc_bench_modmul(3, 0, 512, 4, sink)
+    torch.cuda.synchronize()
+    with pytest.raises(ecc.EccError):
+        gpu_lib.ecc_bench_modmul(3, 1, 512, 4, sink)
