@@ -230,12 +230,8 @@ ECC_DEV void fe_shfl_xor(uint32_t* r, const uint32_t* a, int mask) {
   for (int i = 0; i < F::N; ++i) r[i] = __shfl_xor_sync(0xffffffffu, a[i], mask);
 }
 
-// Out of line: it runs once per round, and one copy per field serves every
-// round type of a kernel instead of one inlined tree (16 products) each, which
-// keeps the kernels' hot code within the instruction cache.
 template <class F, int BLOCK>
-__device__ __noinline__ void cta_invert(uint32_t* out, const uint32_t* in,
-                                        GasSmem<F::N, BLOCK>& sm) {
+__device__ void cta_invert(uint32_t* out, const uint32_t* in, GasSmem<F::N, BLOCK>& sm) {
   constexpr int N = F::N;
   constexpr int NW = BLOCK / 32;
   const int tid = threadIdx.x;
