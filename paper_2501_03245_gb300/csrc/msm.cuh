@@ -328,6 +328,7 @@ struct FoldArgs {
   uint32_t n_buckets;
   PtSoA<F> partial;
   SoA<F> M;                     // GAS prefix products, one per slot
+  uint32_t* ops;                // per-round list of additions, one word per slot
 };
 
 // first b in [0, n] with poff[b] >= x
@@ -363,22 +364,56 @@ struct FoldOp {
   }
 };
 
-// Items are buckets: in each round a thread performs all pair additions of its
-// buckets (one for a bucket of two or three partials), so lanes stay converged
-// unless a bucket holds many partials.
+// Exclusive prefix sum of v over the CTA (warp shuffles, then the warp
+// totals); total gets the CTA sum.  wsum: BLOCK / 32 shared words.
+template <int BLOCK>
+ECC_DEV uint32_t cta_exclusive_sum(uint32_t v, uint32_t* wsum, uint32_t& total) {
+  constexpr int NW = BLOCK / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < NW ? wsum[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < NW) wsum[lane] = w;
+  }
+  __syncthreads();
+  const uint32_t before = warp > 0 ? wsum[warp - 1] : 0u;
+  total = wsum[NW - 1];
+  __syncthreads();  // wsum is reused
+  return before + x - v;
+}
+
+// Each round first lists the CTA's pair additions (slot of the left operand)
+// in ops[s0 ..), then runs the batched additions over that list, so the work
+// of a bucket with many partial sums (the top window often puts most entries
+// into a few buckets) is shared by the whole CTA and lanes never idle on
+// inactive slots.
 template <class C, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, kGasResidentThreads / BLOCK) k_msm_fold(FoldArgs<C> a) {
   using F = typename C::Fp;
   constexpr int N = F::N;
   auto& sm = gas_smem<N, BLOCK>();
-  const uint64_t total = a.poff[a.n_buckets];
-  if (total == 0) return;  // uniform over the grid
+  __shared__ uint32_t wsum[BLOCK / 32];
+  const uint64_t total_slots = a.poff[a.n_buckets];
+  if (total_slots == 0) return;  // uniform over the grid
   // this CTA owns the buckets whose first slot lies in its equal share
-  const uint64_t share = (total + gridDim.x - 1) / gridDim.x;
+  const uint64_t share = (total_slots + gridDim.x - 1) / gridDim.x;
   const uint32_t b0 = lower_bound_u32(a.poff, a.n_buckets, blockIdx.x * share);
   const uint32_t b1 = blockIdx.x + 1 == gridDim.x
                           ? a.n_buckets
                           : lower_bound_u32(a.poff, a.n_buckets, (blockIdx.x + 1) * share);
+  const uint64_t s0 = a.poff[b0];
   uint32_t kmax = 0;
   for (uint32_t b = b0 + threadIdx.x; b < b1; b += BLOCK) {
     const uint32_t k = a.poff[b + 1] - a.poff[b];
@@ -386,38 +421,43 @@ __global__ void __launch_bounds__(BLOCK, kGasResidentThreads / BLOCK) k_msm_fold
   }
   // ceil(log2 kmax) rounds; each halves the partials of every bucket
   for (uint32_t h = 1; __syncthreads_or(h < kmax); h *= 2) {
+    // list the round's additions: l = 0, 2h, 4h, .. with l + h < k
+    uint32_t cnt = 0;
+    for (uint32_t b = b0 + threadIdx.x; b < b1; b += BLOCK) {
+      const uint32_t k = a.poff[b + 1] - a.poff[b];
+      if (k > h) cnt += (k - h - 1) / (2 * h) + 1;
+    }
+    uint32_t n_ops;
+    uint32_t pos = cta_exclusive_sum<BLOCK>(cnt, wsum, n_ops);
+    for (uint32_t b = b0 + threadIdx.x; b < b1; b += BLOCK) {
+      const uint32_t p = a.poff[b];
+      const uint32_t k = a.poff[b + 1] - p;
+      for (uint32_t l = 0; l + h < k; l += 2 * h) a.ops[s0 + pos++] = p + l;
+    }
+    __syncthreads();  // the list is complete
     FoldOp<C> op{&a, h};
     uint32_t run[N];
     fe_set_one<F>(run);
-    for (uint32_t b = b0 + threadIdx.x; b < b1; b += BLOCK) {
-      const uint64_t p = a.poff[b];
-      const uint32_t k = (uint32_t)(a.poff[b + 1] - p);
-      for (uint32_t l = 0; l + h < k; l += 2 * h) {
-        uint32_t d[N];
-        a.M.store(p + l, run);
-        op.den(p + l, d);
-        mont_mul<F>(run, run, d);
-      }
+    for (uint32_t e = threadIdx.x; e < n_ops; e += BLOCK) {
+      const uint32_t s = a.ops[s0 + e];
+      uint32_t d[N];
+      a.M.store(s, run);
+      op.den(s, d);
+      mont_mul<F>(run, run, d);
     }
     uint32_t inv[N];
     cta_invert<F, BLOCK>(inv, run, sm);
-    if (b0 + threadIdx.x < b1) {
-      const uint32_t first = b0 + threadIdx.x;
-      const uint32_t last = first + ((b1 - 1 - first) / BLOCK) * BLOCK;
-      for (uint32_t b = last + BLOCK; b > first;) {
-        b -= BLOCK;
-        const uint64_t p = a.poff[b];
-        const uint32_t k = (uint32_t)(a.poff[b + 1] - p);
-        if (k <= h) continue;
-        for (uint32_t l = ((k - h - 1) / (2 * h)) * (2 * h);; l -= 2 * h) {
-          uint32_t d[N], pre[N], mine[N];
-          const int kind = op.den(p + l, d);
-          a.M.load(p + l, pre);
-          mont_mul<F>(mine, inv, pre);
-          mont_mul<F>(inv, inv, d);
-          op.finish(p + l, kind, mine);
-          if (l == 0) break;
-        }
+    if (threadIdx.x < n_ops) {
+      const uint32_t last = threadIdx.x + ((n_ops - 1 - threadIdx.x) / BLOCK) * BLOCK;
+      for (uint32_t e = last + BLOCK; e > threadIdx.x;) {
+        e -= BLOCK;
+        const uint32_t s = a.ops[s0 + e];
+        uint32_t d[N], pre[N], mine[N];
+        const int kind = op.den(s, d);
+        a.M.load(s, pre);
+        mont_mul<F>(mine, inv, pre);
+        mont_mul<F>(inv, inv, d);
+        op.finish(s, kind, mine);
       }
     }
   }

@@ -49,7 +49,8 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
   const uint64_t sz_b1 = up((B + 1) * 4);
   const uint64_t sz_kv = up(kAccChunk * NC * 4), sz_cur = up(NC * 4);
   const uint64_t sz_S = soa_bytes<F>(NC), sz_P = soa_bytes<F>(n_part);
-  const uint64_t bytes = sz_inst + 5 * sz_b1 + sz_kv + sz_cur + 4 * sz_S + 3 * sz_P + 256;
+  const uint64_t sz_ops = up(n_part * 4);
+  const uint64_t bytes = sz_inst + 5 * sz_b1 + sz_kv + sz_cur + 4 * sz_S + 3 * sz_P + sz_ops + 256;
   Scratch ws;
   cudaError_t e = ws.alloc(bytes, st);
   if (e != cudaSuccess) return e;
@@ -65,6 +66,7 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
   uint32_t* cur = reinterpret_cast<uint32_t*>(take(sz_cur));
   uint4* sbuf = reinterpret_cast<uint4*>(take(4 * sz_S));
   uint4* pbuf = reinterpret_cast<uint4*>(take(3 * sz_P));
+  uint32_t* fold_ops = reinterpret_cast<uint32_t*>(take(sz_ops));
   e = upload_words(d_inst, L.inst.data(), num * sizeof(MsmInst), st);
   if (e != cudaSuccess) return e;
   // ---- 1-2: digits, counting sort by bucket id
@@ -113,6 +115,7 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
     f.n_buckets = (uint32_t)B;
     f.partial = a.partial;
     f.M = SoA<F>{pbuf + 2 * sz_P / 16, n_part};
+    f.ops = fold_ops;
     e = cudaFuncSetAttribute(k_msm_fold<C, kAccBlock>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

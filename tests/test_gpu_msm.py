@@ -135,3 +135,25 @@ def test_msm_unsupported_curve(gpu_lib):
     with pytest.raises(gpu_lib.EccError) as e:
         gpu_lib.ecc_msm(0, 4, a, a, a)
     assert e.value.code == gpu_lib.ECC_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("cid,n,c,same", [(3, 4096, 15, False), (2, 8192, 0, True)])
+def test_msm_heavy_buckets(gpu_lib, cid, n, c, same):
+    """Buckets holding hundreds of partial sums: BLS12-381 at c = 15 (the top
+    window holds only the carry, so about half the points share one bucket) and
+    BN254 with every scalar equal (each window's only bucket holds all n)."""
+    C = curves.BY_ID[cid]
+    pts, _ = random_points(C, n, 0x6ECC1300 + cid)
+    _, ks = synth.msm_raw(0x6ECC1400 + cid, n, C.n, 1)
+    k_l = ks[0]
+    if same:
+        k_l = np.repeat(k_l[:1], n, axis=0)
+    pts_l = _pts_limbs(C, pts)
+    log2n = n.bit_length() - 1
+    if c:
+        gpu_lib.ecc_msm_set_window(cid, log2n, c)
+    try:
+        assert _gpu_msm(gpu_lib, cid, pts_l, k_l) == _oracle_msm(cid, pts_l, k_l)
+    finally:
+        if c:
+            gpu_lib.ecc_msm_set_window(cid, log2n, 0)
