@@ -215,7 +215,8 @@ def bench_msm(ecc, costmodel, synth, torch, peak, rank, n=1 << 20, V=16):
     from paper_2501_03245_gb300 import autotune
 
     curve = ecc.ECC_BLS12_381
-    tuned = autotune.tune(curve, [n.bit_length() - 1], torch)  # measured window width for n's class
+    # measured window width for n's class, on this call's shape (V vectors)
+    tuned = autotune.tune(curve, [n.bit_length() - 1], torch, vectors=V)
     seed = synth.SEED_BASE + 2 + 1000 * rank
     a, ks = synth.msm_raw(seed, n, BLS_R, V)
     pts = torch.empty((n, 24), dtype=torch.int32, device="cuda")

@@ -43,19 +43,39 @@ def time_msm(curve, bases, scalars, n, torch, reps=3):
     return a.elapsed_time(b) / reps / 1e3
 
 
-def tune(curve, log2_sizes, torch, spread=2, seed=0x6ECC7777, cache=None):
-    """Returns {log2_n: c} and installs it in the library."""
+def time_msm_bases(curve, bases, scalars, n, vectors, torch, reps=3):
+    """Time of one ecc_msm_bases call over `vectors` scalar vectors of n."""
+    h = ecc.ecc_bases_create(curve, n, bases)
+    try:
+        out = torch.empty((vectors, 2 * ecc.ecc_limbs(curve)), dtype=torch.int32, device="cuda")
+        ecc.ecc_msm_bases(h, vectors, scalars, out)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            ecc.ecc_msm_bases(h, vectors, scalars, out)
+        b.record()
+        torch.cuda.synchronize()
+    finally:
+        ecc.ecc_bases_destroy(h)
+    return a.elapsed_time(b) / reps / 1e3
+
+
+def tune(curve, log2_sizes, torch, spread=2, seed=0x6ECC7777, cache=None, vectors=1):
+    """Returns {log2_n: c} and installs it in the library.  With vectors > 1
+    every candidate is timed on the resident-bases form with that many scalar
+    vectors per call (the best window grows with the vectors sharing a call)."""
     key = None
     table = {}
     if cache and os.path.exists(cache):
-        key = f"{torch.cuda.get_device_name()}|{curve}"
+        key = f"{torch.cuda.get_device_name()}|{curve}|{vectors}"
         saved = json.load(open(cache)).get(key, {})
         table = {int(k): int(v) for k, v in saved.items()}
     missing = [l for l in log2_sizes if l not in table]
     if missing:
         n_max = 1 << max(missing)
         bases = make_bases(curve, n_max, seed, torch)
-        ks = synth.uniform_limbs(seed, synth.S_SCALAR, n_max, _curve_order(curve))
+        ks = synth.uniform_limbs(seed, synth.S_SCALAR, n_max * vectors, _curve_order(curve))
         scalars = torch.from_numpy(ks.view("int32")).cuda()
         for l in missing:
             n = 1 << l
@@ -64,14 +84,17 @@ def tune(curve, log2_sizes, torch, spread=2, seed=0x6ECC7777, cache=None):
             best = None
             for c in range(max(2, c0 - spread), min(20, c0 + spread) + 1):
                 ecc.ecc_msm_set_window(curve, l, c)
-                t = time_msm(curve, bases, scalars, n, torch)
+                if vectors > 1:
+                    t = time_msm_bases(curve, bases, scalars[:n * vectors].contiguous(), n, vectors, torch)
+                else:
+                    t = time_msm(curve, bases, scalars, n, torch)
                 if best is None or t < best[0]:
                     best = (t, c)
             table[l] = best[1]
     for l, c in table.items():
         ecc.ecc_msm_set_window(curve, l, c)
     if cache:
-        key = key or f"{torch.cuda.get_device_name()}|{curve}"
+        key = key or f"{torch.cuda.get_device_name()}|{curve}|{vectors}"
         data = json.load(open(cache)) if os.path.exists(cache) else {}
         data[key] = {str(k): v for k, v in sorted(table.items())}
         with open(cache, "w") as f:
