@@ -47,7 +47,8 @@ typedef enum {
   ECC_SECP256K1 = 0,    /* SEC 2 secp256k1: a = 0, b = 7 */
   ECC_P256 = 1,         /* NIST P-256 (secp256r1): a = -3 */
   ECC_BN254 = 2,        /* BN254 G1: a = 0, b = 3 */
-  ECC_BLS12_381 = 3     /* BLS12-381 G1: a = 0, b = 4, 381-bit base field */
+  ECC_BLS12_381 = 3,    /* BLS12-381 G1: a = 0, b = 4, 381-bit base field */
+  ECC_SM2 = 4           /* SM2 recommended curve (GB/T 32918.5, the paper's curve): a = -3 */
 } ecc_curve_t;
 
 enum {
@@ -135,7 +136,7 @@ int ecc_point_dbl_batch(ecc_curve_t curve, size_t n, const uint32_t* p, uint32_t
 
 /* ---------------------------------------------------------------- ECDSA
  * Batched ECDSA verification (Section 5.2; SEC 1 section 4.1.4).
- * curve: ECC_SECP256K1 or ECC_P256 (others: ECC_EUNSUPPORTED).
+ * curve: ECC_SECP256K1, ECC_P256 or ECC_SM2 (others: ECC_EUNSUPPORTED).
  * hash, r, s: n x 32 bytes, big-endian integers (the hash is used as e without
  * truncation: both group orders are 256-bit).
  * pubkey: n x 64 bytes, x || y big-endian, uncompressed, no 0x04 prefix.
@@ -156,7 +157,7 @@ int ecc_fixed_base_mul(ecc_curve_t curve, size_t n, const uint32_t* k, uint32_t*
 /* Batched ECDSA signing (Section 5.2: one modinv plus one FPMUL; SEC 1 section
  * 4.1.3 with the nonce supplied by the caller): r = x(k G) mod n,
  * s = k^-1 (e + r d) mod n, and the public key d G.
- * curve: ECC_SECP256K1 or ECC_P256.  d, e, k: n x 32 bytes big-endian;
+ * curve: ECC_SECP256K1, ECC_P256 or ECC_SM2.  d, e, k: n x 32 bytes big-endian;
  * r_out, s_out: n x 32 bytes; pub_out: n x 64 bytes (x || y).  An item with d
  * or k outside [1, n-1], or whose nonce gives r = 0 or s = 0, gets r = s = 0. */
 int ecc_sign_batch(ecc_curve_t curve, size_t n, const uint8_t* d, const uint8_t* e,

@@ -356,8 +356,9 @@ struct CurveHex {
 };
 
 // Standard parameters (SEC 2 for secp256k1 and secp256r1 = P-256; BN254 G1 from
-// u = 0x44E992B44A6909F1; BLS12-381 G1 from x = -0xd201000000010000).
-const CurveHex kCurves[4] = {
+// u = 0x44E992B44A6909F1; BLS12-381 G1 from x = -0xd201000000010000; the SM2
+// recommended curve of GB/T 32918.5).
+const CurveHex kCurves[5] = {
     {8, "fffffffffffffffffffffffffffffffffffffffffffffffffffffffefffffc2f", "0", "7",
      "79be667ef9dcbbac55a06295ce870b07029bfcdb2dce28d959f2815b16f81798",
      "483ada7726a3c4655da4fbfc0e1108a8fd17b448a68554199c47d08ffb10d4b8",
@@ -376,9 +377,15 @@ const CurveHex kCurves[4] = {
      "17f1d3a73197d7942695638c4fa9ac0fc3688c4f9774b905a14e3a3f171bac586c55e83ff97a1aeffb3af00adb22c6bb",
      "08b3f481e3aaa0f1a09e30ed741d8ae4fcf5e095d5d00af600db18cb2c04b3edd03cc744a2888ae40caa232946c5e7e1",
      "73eda753299d7d483339d80809a1d80553bda402fffe5bfeffffffff00000001"},
+    {8, "fffffffeffffffffffffffffffffffffffffffff00000000ffffffffffffffff",
+     "fffffffeffffffffffffffffffffffffffffffff00000000fffffffffffffffc",
+     "28e9fa9e9d9f5e344d5a9e4bcf6509a7f39789f515ab8f92ddbcbd414d940e93",
+     "32c4ae2c1f1981195f9904466a39c9948fe30bbff2660be1715a4589334c74c7",
+     "bc3736a2f4f6779c59bdcee36b692153d0a9877cc62a474002df32e52139f0a0",
+     "fffffffeffffffffffffffffffffffff7203df6b21c6052b53bbf40939d54123"},
 };
 
-CurveDef g_curves[4];
+CurveDef g_curves[5];
 std::atomic<bool> g_ready{false};
 
 void init_curves() {
@@ -387,7 +394,7 @@ void init_curves() {
   while (busy.test_and_set()) {
   }
   if (!g_ready.load()) {
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < 5; ++c) {
       const CurveHex& h = kCurves[c];
       uint32_t t[MAXL];
       parse_hex(t, h.m, h.p);
@@ -496,7 +503,7 @@ extern "C" {
 // Returns 0 on success, -1 on a bad curve id.
 int orc_verify(int curve, size_t n, const uint8_t* hash, const uint8_t* r, const uint8_t* s,
                const uint8_t* pub, uint8_t* ok, int threads) {
-  if (curve < 0 || curve > 1) return -1;
+  if (curve != 0 && curve != 1 && curve != 4) return -1;
   init_curves();
   const CurveDef& C = g_curves[curve];
   parallel_for(n, threads, [&](size_t i, int) {
@@ -510,7 +517,7 @@ int orc_verify(int curve, size_t n, const uint8_t* hash, const uint8_t* r, const
 // nonce gives r = 0 or s = 0 gets r = s = 0 (the caller redraws).
 int orc_sign(int curve, size_t n, const uint8_t* d, const uint8_t* e, const uint8_t* k,
              uint8_t* r_out, uint8_t* s_out, uint8_t* pub_out, int threads) {
-  if (curve < 0 || curve > 1) return -1;
+  if (curve != 0 && curve != 1 && curve != 4) return -1;
   init_curves();
   const CurveDef& C = g_curves[curve];
   parallel_for(n, threads, [&](size_t i, int) {
@@ -544,7 +551,7 @@ int orc_sign(int curve, size_t n, const uint8_t* d, const uint8_t* e, const uint
 // out_i = k_i * P_i (affine, (0,0) for O).  Scalars: 8 limbs; points: 2m limbs.
 int orc_scalar_mul(int curve, size_t n, const uint32_t* k, const uint32_t* pts, uint32_t* out,
                    int threads) {
-  if (curve < 0 || curve > 3) return -1;
+  if (curve < 0 || curve > 4) return -1;
   init_curves();
   const CurveDef& C = g_curves[curve];
   const int m = C.fp.m;
@@ -568,7 +575,7 @@ int orc_scalar_mul(int curve, size_t n, const uint32_t* k, const uint32_t* pts, 
 // out = sum_i k_i * P_i (affine, (0,0) for O).
 int orc_msm(int curve, size_t n, const uint32_t* pts, const uint32_t* k, uint32_t* out,
             int threads) {
-  if (curve < 0 || curve > 3) return -1;
+  if (curve < 0 || curve > 4) return -1;
   init_curves();
   const CurveDef& C = g_curves[curve];
   const int m = C.fp.m;
@@ -598,7 +605,7 @@ int orc_msm(int curve, size_t n, const uint32_t* pts, const uint32_t* k, uint32_
 // which = 0 for the base field p, 1 for the group order n.
 int orc_fe_mul(int curve, int which, size_t n, const uint32_t* a, const uint32_t* b,
                uint32_t* out) {
-  if (curve < 0 || curve > 3) return -1;
+  if (curve < 0 || curve > 4) return -1;
   init_curves();
   const Field& F = which ? g_curves[curve].fn : g_curves[curve].fp;
   for (size_t i = 0; i < n; ++i) {
@@ -612,7 +619,7 @@ int orc_fe_mul(int curve, int which, size_t n, const uint32_t* a, const uint32_t
 }
 
 int orc_fe_inv(int curve, int which, size_t n, const uint32_t* a, uint32_t* out) {
-  if (curve < 0 || curve > 3) return -1;
+  if (curve < 0 || curve > 4) return -1;
   init_curves();
   const Field& F = which ? g_curves[curve].fn : g_curves[curve].fp;
   for (size_t i = 0; i < n; ++i) {
@@ -625,7 +632,7 @@ int orc_fe_inv(int curve, int which, size_t n, const uint32_t* a, uint32_t* out)
 }
 
 int orc_limbs(int curve) {
-  if (curve < 0 || curve > 3) return -1;
+  if (curve < 0 || curve > 4) return -1;
   return kCurves[curve].m;
 }
 

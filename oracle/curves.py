@@ -85,6 +85,18 @@ BLS12_381 = Curve(
     h=(BLS_X - 1) ** 2 // 3,
 )
 
+_SM2_P = 2**256 - 2**224 - 2**96 + 2**64 - 1
+SM2 = Curve(
+    name="SM2",
+    p=_SM2_P,
+    a=_SM2_P - 3,
+    b=0x28E9FA9E9D9F5E344D5A9E4BCF6509A7F39789F515AB8F92DDBCBD414D940E93,
+    gx=0x32C4AE2C1F1981195F9904466A39C9948FE30BBFF2660BE1715A4589334C74C7,
+    gy=0xBC3736A2F4F6779C59BDCEE36B692153D0A9877CC62A474002DF32E52139F0A0,
+    n=0xFFFFFFFEFFFFFFFFFFFFFFFFFFFFFFFF7203DF6B21C6052B53BBF40939D54123,
+    h=1,
+)
+
 # Curve identifiers shared with the C-ABI enumeration (argument values only).
-BY_ID = {0: SECP256K1, 1: P256, 2: BN254, 3: BLS12_381}
+BY_ID = {0: SECP256K1, 1: P256, 2: BN254, 3: BLS12_381, 4: SM2}
 BY_NAME = {c.name: c for c in BY_ID.values()}

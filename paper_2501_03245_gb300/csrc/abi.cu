@@ -81,7 +81,7 @@ struct Arg {
   }
 };
 
-bool valid_curve(int c) { return c >= 0 && c <= 3; }
+bool valid_curve(int c) { return c >= 0 && c <= 4; }
 
 // Runs `body` with device views of the inputs/outputs; synchronises when any
 // of them was staged from host memory.
@@ -250,8 +250,8 @@ int ecc_verify_batch(ecc_curve_t curve, size_t n, const uint8_t* hash, const uin
                      const uint8_t* s, const uint8_t* pubkey, uint8_t* ok_out, void* stream) {
   const char* name = "ecc_verify_batch";
   if (!valid_curve(curve)) return fail(ECC_EINVAL, "%s: unknown curve %d", name, (int)curve);
-  if (curve != ECC_SECP256K1 && curve != ECC_P256)
-    return fail(ECC_EUNSUPPORTED, "%s: ECDSA is offered on secp256k1 and P-256", name);
+  if (curve != ECC_SECP256K1 && curve != ECC_P256 && curve != ECC_SM2)
+    return fail(ECC_EUNSUPPORTED, "%s: ECDSA is offered on secp256k1, P-256 and SM2", name);
   if (n == 0) return ok();
   if (!hash || !r || !s || !pubkey || !ok_out) return fail(ECC_EINVAL, "%s: NULL pointer", name);
   if (!aligned4(hash) || !aligned4(r) || !aligned4(s) || !aligned4(pubkey))
@@ -287,8 +287,8 @@ int ecc_sign_batch(ecc_curve_t curve, size_t n, const uint8_t* d, const uint8_t*
                    void* stream) {
   const char* name = "ecc_sign_batch";
   if (!valid_curve(curve)) return fail(ECC_EINVAL, "%s: unknown curve %d", name, (int)curve);
-  if (curve != ECC_SECP256K1 && curve != ECC_P256)
-    return fail(ECC_EUNSUPPORTED, "%s: ECDSA is offered on secp256k1 and P-256", name);
+  if (curve != ECC_SECP256K1 && curve != ECC_P256 && curve != ECC_SM2)
+    return fail(ECC_EUNSUPPORTED, "%s: ECDSA is offered on secp256k1, P-256 and SM2", name);
   if (n == 0) return ok();
   if (!d || !e || !k || !r_out || !s_out || !pub_out) return fail(ECC_EINVAL, "%s: NULL pointer", name);
   if (!aligned4(d) || !aligned4(e) || !aligned4(k) || !aligned4(r_out) || !aligned4(s_out) ||

@@ -283,4 +283,72 @@ struct BLS12_381 {
   static constexpr int SCALAR_BITS = 255;
 };
 
+struct SM2Fp {
+  static constexpr int N = 8;
+  static constexpr int BITS = 256;
+  static constexpr uint32_t QINV = 0x00000001u;
+  static constexpr int FORM = 0;
+  static constexpr uint64_t QINV62 = 0x3fffffffffffffffull;  // q^-1 mod 2^62
+  ECC_DEV static constexpr uint32_t p(int i) {
+    switch (i) { case 0: return 0xffffffffu; case 1: return 0xffffffffu; case 2: return 0x00000000u; case 3: return 0xffffffffu; case 4: return 0xffffffffu; case 5: return 0xffffffffu; case 6: return 0xffffffffu; case 7: return 0xfffffffeu; default: return 0u; }
+  }
+  ECC_DEV static constexpr uint32_t r2(int i) {
+    switch (i) { case 0: return 0x00000003u; case 1: return 0x00000002u; case 2: return 0xffffffffu; case 3: return 0x00000002u; case 4: return 0x00000001u; case 5: return 0x00000001u; case 6: return 0x00000002u; case 7: return 0x00000004u; default: return 0u; }
+  }
+  ECC_DEV static constexpr uint32_t one(int i) {
+    switch (i) { case 0: return 0x00000001u; case 1: return 0x00000000u; case 2: return 0xffffffffu; case 3: return 0x00000000u; case 4: return 0x00000000u; case 5: return 0x00000000u; case 6: return 0x00000000u; case 7: return 0x00000001u; default: return 0u; }
+  }
+  ECC_DEV static constexpr uint32_t pm2(int i) {
+    switch (i) { case 0: return 0xfffffffdu; case 1: return 0xffffffffu; case 2: return 0x00000000u; case 3: return 0xffffffffu; case 4: return 0xffffffffu; case 5: return 0xffffffffu; case 6: return 0xffffffffu; case 7: return 0xfffffffeu; default: return 0u; }
+  }
+  ECC_DEV static constexpr uint32_t r3(int i) {
+    switch (i) { case 0: return 0x00000016u; case 1: return 0x00000012u; case 2: return 0xfffffff8u; case 3: return 0x0000000eu; case 4: return 0x0000000cu; case 5: return 0x0000000au; case 6: return 0x00000009u; case 7: return 0x0000001bu; default: return 0u; }
+  }
+};
+
+struct SM2Fn {
+  static constexpr int N = 8;
+  static constexpr int BITS = 256;
+  static constexpr uint32_t QINV = 0x72350975u;
+  static constexpr int FORM = 0;
+  static constexpr uint64_t QINV62 = 0x0d8061778dcaf68bull;  // q^-1 mod 2^62
+  ECC_DEV static constexpr uint32_t p(int i) {
+    switch (i) { case 0: return 0x39d54123u; case 1: return 0x53bbf409u; case 2: return 0x21c6052bu; case 3: return 0x7203df6bu; case 4: return 0xffffffffu; case 5: return 0xffffffffu; case 6: return 0xffffffffu; case 7: return 0xfffffffeu; default: return 0u; }
+  }
+  ECC_DEV static constexpr uint32_t r2(int i) {
+    switch (i) { case 0: return 0x7c114f20u; case 1: return 0x901192afu; case 2: return 0xde6fa2fau; case 3: return 0x3464504au; case 4: return 0x3affe0d4u; case 5: return 0x620fc84cu; case 6: return 0xa22b3d3bu; case 7: return 0x1eb5e412u; default: return 0u; }
+  }
+  ECC_DEV static constexpr uint32_t one(int i) {
+    switch (i) { case 0: return 0xc62abeddu; case 1: return 0xac440bf6u; case 2: return 0xde39fad4u; case 3: return 0x8dfc2094u; case 4: return 0x00000000u; case 5: return 0x00000000u; case 6: return 0x00000000u; case 7: return 0x00000001u; default: return 0u; }
+  }
+  ECC_DEV static constexpr uint32_t pm2(int i) {
+    switch (i) { case 0: return 0x39d54121u; case 1: return 0x53bbf409u; case 2: return 0x21c6052bu; case 3: return 0x7203df6bu; case 4: return 0xffffffffu; case 5: return 0xffffffffu; case 6: return 0xffffffffu; case 7: return 0xfffffffeu; default: return 0u; }
+  }
+  ECC_DEV static constexpr uint32_t r3(int i) {
+    switch (i) { case 0: return 0x0eaa0b85u; case 1: return 0x6ff874c7u; case 2: return 0xaabe8d32u; case 3: return 0x87d0c315u; case 4: return 0x97185afcu; case 5: return 0x4c4fbbb3u; case 6: return 0xd574ea14u; case 7: return 0xc813249cu; default: return 0u; }
+  }
+};
+
+struct SM2 {
+  using Fp = SM2Fp;
+  using Fn = SM2Fn;
+  static constexpr bool A_ZERO = false;
+  ECC_DEV static constexpr uint32_t a(int i) {
+    switch (i) { case 0: return 0xfffffffcu; case 1: return 0xffffffffu; case 2: return 0x00000003u; case 3: return 0xfffffffcu; case 4: return 0xffffffffu; case 5: return 0xffffffffu; case 6: return 0xffffffffu; case 7: return 0xfffffffbu; default: return 0u; }
+  }
+  ECC_DEV static constexpr uint32_t b(int i) {
+    switch (i) { case 0: return 0x2bc0dd42u; case 1: return 0x90d23063u; case 2: return 0xe9b537abu; case 3: return 0x71cf379au; case 4: return 0x5ea51c3cu; case 5: return 0x52798150u; case 6: return 0xba20e2c8u; case 7: return 0x240fe188u; default: return 0u; }
+  }
+  ECC_DEV static constexpr uint32_t gx(int i) {
+    switch (i) { case 0: return 0x334c74c7u; case 1: return 0x715a4589u; case 2: return 0xf2660be1u; case 3: return 0x8fe30bbfu; case 4: return 0x6a39c994u; case 5: return 0x5f990446u; case 6: return 0x1f198119u; case 7: return 0x32c4ae2cu; default: return 0u; }
+  }
+  ECC_DEV static constexpr uint32_t gy(int i) {
+    switch (i) { case 0: return 0x2139f0a0u; case 1: return 0x02df32e5u; case 2: return 0xc62a4740u; case 3: return 0xd0a9877cu; case 4: return 0x6b692153u; case 5: return 0x59bdcee3u; case 6: return 0xf4f6779cu; case 7: return 0xbc3736a2u; default: return 0u; }
+  }
+  ECC_DEV static constexpr uint32_t n(int i) {
+    switch (i) { case 0: return 0x39d54123u; case 1: return 0x53bbf409u; case 2: return 0x21c6052bu; case 3: return 0x7203df6bu; case 4: return 0xffffffffu; case 5: return 0xffffffffu; case 6: return 0xffffffffu; case 7: return 0xfffffffeu; default: return 0u; }
+  }
+  static constexpr int SCALAR_BITS = 256;
+};
+
 }  // namespace ecc

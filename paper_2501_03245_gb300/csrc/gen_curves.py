@@ -7,7 +7,7 @@ Run from this directory: ``python gen_curves.py`` (the output is committed).
 The parameters are the published standard ones: SEC 2 (secp256k1,
 secp256r1 = NIST P-256), the BN254 polynomial in u = 0x44E992B44A6909F1 with
 b = 3 and generator (1, 2), and BLS12-381 (x = -0xd201000000010000, b = 4, the
-standard G1 generator).
+standard G1 generator), and the SM2 recommended curve of GB/T 32918.5.
 """
 import os
 
@@ -33,6 +33,12 @@ CURVES = [
      0x17F1D3A73197D7942695638C4FA9AC0FC3688C4F9774B905A14E3A3F171BAC586C55E83FF97A1AEFFB3AF00ADB22C6BB,
      0x08B3F481E3AAA0F1A09E30ED741D8AE4FCF5E095D5D00AF600DB18CB2C04B3EDD03CC744A2888AE40CAA232946C5E7E1,
      0x73EDA753299D7D483339D80809A1D80553BDA402FFFE5BFEFFFFFFFF00000001),
+    ("SM2",
+     0xFFFFFFFEFFFFFFFFFFFFFFFFFFFFFFFFFFFFFFFF00000000FFFFFFFFFFFFFFFF, -3,
+     0x28E9FA9E9D9F5E344D5A9E4BCF6509A7F39789F515AB8F92DDBCBD414D940E93,
+     0x32C4AE2C1F1981195F9904466A39C9948FE30BBFF2660BE1715A4589334C74C7,
+     0xBC3736A2F4F6779C59BDCEE36B692153D0A9877CC62A474002DF32E52139F0A0,
+     0xFFFFFFFEFFFFFFFFFFFFFFFFFFFFFFFF7203DF6B21C6052B53BBF40939D54123),
 ]
 
 

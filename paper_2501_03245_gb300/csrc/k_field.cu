@@ -188,6 +188,8 @@ int field_limbs(int curve, int field) {
     case 5: { using F = BN254Fn; return CALL; }         \
     case 6: { using F = BLS12_381Fp; return CALL; }     \
     case 7: { using F = BLS12_381Fn; return CALL; }     \
+    case 8: { using F = SM2Fp; return CALL; }           \
+    case 9: { using F = SM2Fn; return CALL; }           \
   }                                                     \
   return cudaErrorInvalidValue;
 
@@ -233,6 +235,7 @@ cudaError_t launch_bench_inv(int curve, int method, size_t threads, int iters, u
     case 1: k_bench_inv<P256Fp><<<b, t, 0, st>>>(method, iters, sink); break;
     case 2: k_bench_inv<BN254Fp><<<b, t, 0, st>>>(method, iters, sink); break;
     case 3: k_bench_inv<BLS12_381Fp><<<b, t, 0, st>>>(method, iters, sink); break;
+    case 4: k_bench_inv<SM2Fp><<<b, t, 0, st>>>(method, iters, sink); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -251,6 +254,7 @@ cudaError_t launch_bench_modmul(int curve, int reduction, size_t threads, int it
     case 1: k_bench_modmul<P256Fp><<<b, 256, 0, st>>>(iters, sink); break;
     case 2: k_bench_modmul<BN254Fp><<<b, 256, 0, st>>>(iters, sink); break;
     case 3: k_bench_modmul<BLS12_381Fp><<<b, 256, 0, st>>>(iters, sink); break;
+    case 4: k_bench_modmul<SM2Fp><<<b, 256, 0, st>>>(iters, sink); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -70,6 +70,7 @@ cudaError_t launch_fixed_base_mul(int curve, size_t n, const uint32_t* k, uint32
     case 1: return fixed_base<P256>(1, 0, n, k, nullptr, nullptr, out, nullptr, nullptr, nullptr, st);
     case 2: return fixed_base<BN254>(2, 0, n, k, nullptr, nullptr, out, nullptr, nullptr, nullptr, st);
     case 3: return fixed_base<BLS12_381>(3, 0, n, k, nullptr, nullptr, out, nullptr, nullptr, nullptr, st);
+    case 4: return fixed_base<SM2>(4, 0, n, k, nullptr, nullptr, out, nullptr, nullptr, nullptr, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -81,6 +82,7 @@ cudaError_t launch_sign(int curve, size_t n, const uint8_t* d, const uint8_t* e,
   switch (curve) {
     case 0: return fixed_base<Secp256k1>(0, 1, n, w(k), w(d), w(e), nullptr, o(r), o(s), o(pub), st);
     case 1: return fixed_base<P256>(1, 1, n, w(k), w(d), w(e), nullptr, o(r), o(s), o(pub), st);
+    case 4: return fixed_base<SM2>(4, 1, n, w(k), w(d), w(e), nullptr, o(r), o(s), o(pub), st);
   }
   return cudaErrorNotSupported;
 }

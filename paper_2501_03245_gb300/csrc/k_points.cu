@@ -137,7 +137,7 @@ cudaError_t build_gtable(uint4** out, cudaStream_t st) {
 }
 
 std::mutex g_tab_mu;
-uint4* g_tabs[64][4] = {};
+uint4* g_tabs[64][5] = {};
 
 }  // namespace
 
@@ -145,7 +145,7 @@ cudaError_t gtable(int curve, const uint4** table, cudaStream_t st) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 64 || curve < 0 || curve > 3) return cudaErrorInvalidValue;
+  if (dev < 0 || dev >= 64 || curve < 0 || curve > 4) return cudaErrorInvalidValue;
   std::lock_guard<std::mutex> lock(g_tab_mu);
   if (!g_tabs[dev][curve]) {
     uint4* t = nullptr;
@@ -154,6 +154,7 @@ cudaError_t gtable(int curve, const uint4** table, cudaStream_t st) {
       case 1: e = build_gtable<P256>(&t, st); break;
       case 2: e = build_gtable<BN254>(&t, st); break;
       case 3: e = build_gtable<BLS12_381>(&t, st); break;
+      case 4: e = build_gtable<SM2>(&t, st); break;
     }
     if (e != cudaSuccess) return e;
     g_tabs[dev][curve] = t;
@@ -169,6 +170,7 @@ cudaError_t launch_point_add(int curve, size_t n, const uint32_t* p, const uint3
     case 1: return point_add<P256>(n, p, q, out, dbl, st);
     case 2: return point_add<BN254>(n, p, q, out, dbl, st);
     case 3: return point_add<BLS12_381>(n, p, q, out, dbl, st);
+    case 4: return point_add<SM2>(n, p, q, out, dbl, st);
   }
   return cudaErrorInvalidValue;
 }

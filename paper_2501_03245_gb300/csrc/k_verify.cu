@@ -64,6 +64,7 @@ cudaError_t launch_verify(int curve, size_t n, const uint8_t* hash, const uint8_
   switch (curve) {
     case 0: return verify<Secp256k1>(n, hash, r, s, pub, ok, st, 0);
     case 1: return verify<P256>(n, hash, r, s, pub, ok, st, 1);
+    case 4: return verify<SM2>(n, hash, r, s, pub, ok, st, 4);
   }
   return cudaErrorNotSupported;
 }

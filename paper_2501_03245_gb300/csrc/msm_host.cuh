@@ -24,6 +24,7 @@ inline int scalar_bits(int curve) {
     case 0: return Secp256k1::SCALAR_BITS;
     case 1: return P256::SCALAR_BITS;
     case 2: return BN254::SCALAR_BITS;
+    case 4: return SM2::SCALAR_BITS;
     default: return BLS12_381::SCALAR_BITS;
   }
 }

@@ -14,7 +14,7 @@ import threading
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgecc.so")
 
-ECC_SECP256K1, ECC_P256, ECC_BN254, ECC_BLS12_381 = 0, 1, 2, 3
+ECC_SECP256K1, ECC_P256, ECC_BN254, ECC_BLS12_381, ECC_SM2 = 0, 1, 2, 3, 4
 CURVES = {"secp256k1": 0, "P-256": 1, "BN254": 2, "BLS12-381": 3}
 ECC_FIELD_BASE, ECC_FIELD_SCALAR = 0, 1
 ECC_OK, ECC_EINVAL, ECC_EUNSUPPORTED, ECC_ENOMEM, ECC_ECUDA, ECC_ETIMEOUT = 0, -1, -2, -3, -4, -5

@@ -51,7 +51,7 @@ def test_host_only_calls(lib):
     from paper_2501_03245_gb300 import ecc
 
     lib.ecc_limbs.restype = ctypes.c_int
-    assert lib.ecc_limbs(0) == 8 and lib.ecc_limbs(3) == 12
+    assert lib.ecc_limbs(0) == 8 and lib.ecc_limbs(3) == 12 and lib.ecc_limbs(4) == 8
     assert lib.ecc_limbs(7) == ecc.ECC_EINVAL
     lib.ecc_last_error.restype = ctypes.c_char_p
     assert b"unknown curve" in lib.ecc_last_error()

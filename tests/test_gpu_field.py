@@ -11,7 +11,7 @@ from tests.helpers import from_cuda, to_cuda
 
 pytestmark = pytest.mark.gpu
 
-CASES = [(cid, f) for cid in range(4) for f in (0, 1)]
+CASES = [(cid, f) for cid in range(5) for f in (0, 1)]
 
 
 def _modulus(cid, f):

@@ -10,7 +10,7 @@ from tests.helpers import from_cuda, limbs_to_points, to_cuda
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("cid", [0, 1, 2, 3])
+@pytest.mark.parametrize("cid", [0, 1, 2, 3, 4])
 def test_fixed_base_mul(gpu_lib, cid):
     import torch
 
@@ -33,7 +33,7 @@ def test_fixed_base_mul(gpu_lib, cid):
     assert got[2] == ec.neg(C, C.G)
 
 
-@pytest.mark.parametrize("cid", [0, 1])
+@pytest.mark.parametrize("cid", [0, 1, 4])
 def test_sign_batch(gpu_lib, cid):
     import torch
 

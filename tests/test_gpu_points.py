@@ -9,7 +9,7 @@ from tests.helpers import from_cuda, limbs_to_points, points_to_limbs, random_po
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("cid", [0, 1, 2, 3])
+@pytest.mark.parametrize("cid", [0, 1, 2, 3, 4])
 def test_point_add_dbl(gpu_lib, cid):
     import torch
 

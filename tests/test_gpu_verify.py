@@ -46,7 +46,7 @@ def run_gpu(gpu_lib, cid, e, r, s, pub):
     return from_cuda(ok)
 
 
-@pytest.mark.parametrize("cid", [0, 1])
+@pytest.mark.parametrize("cid", [0, 1, 4])
 def test_verify_small_with_malformed(gpu_lib, cid):
     e, r, s, pub = make_triples(cid, 700, 0x6ECC0500 + cid, 8)
     e, r, s, pub = add_malformed(cid, e, r, s, pub)

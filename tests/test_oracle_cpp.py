@@ -9,7 +9,7 @@ from oracle import curves, ec, ecdsa
 from paper_2501_03245_gb300 import synth
 
 
-@pytest.mark.parametrize("cid", [0, 1, 2, 3])
+@pytest.mark.parametrize("cid", [0, 1, 2, 3, 4])
 def test_field_mul_inv(cpp_oracle, cid):
     C = curves.BY_ID[cid]
     rng = random.Random(cid)
@@ -24,7 +24,7 @@ def test_field_mul_inv(cpp_oracle, cid):
         assert inv == [pow(a, -1, mod) if a else 0 for a in vals_a]
 
 
-@pytest.mark.parametrize("cid", [0, 1, 2, 3])
+@pytest.mark.parametrize("cid", [0, 1, 2, 3, 4])
 def test_scalar_mul_and_msm(cpp_oracle, cid):
     C = curves.BY_ID[cid]
     m = C.limbs
@@ -46,7 +46,7 @@ def test_scalar_mul_and_msm(cpp_oracle, cid):
     assert (synth.limbs_to_int(o[:m]), synth.limbs_to_int(o[m:])) == want
 
 
-@pytest.mark.parametrize("cid", [0, 1])
+@pytest.mark.parametrize("cid", [0, 1, 4])
 def test_sign_verify_agree(cpp_oracle, cid):
     C = curves.BY_ID[cid]
     raw = synth.ecdsa_raw(0x6ECC0200 + cid, 48, C.n, 3)

@@ -33,9 +33,9 @@ def test_generator_on_curve_and_order(C):
 
 
 def test_bit_lengths():
-    assert [c.p.bit_length() for c in ALL] == [256, 256, 254, 381]
-    assert [c.n.bit_length() for c in ALL] == [256, 256, 254, 255]
-    assert [c.limbs for c in ALL] == [8, 8, 8, 12]
+    assert [c.p.bit_length() for c in ALL] == [256, 256, 254, 381, 256]
+    assert [c.n.bit_length() for c in ALL] == [256, 256, 254, 255, 256]
+    assert [c.limbs for c in ALL] == [8, 8, 8, 12, 8]
 
 
 def test_special_forms():
@@ -87,7 +87,8 @@ def _openssl_params(name):
 
 
 @pytest.mark.skipif(shutil.which("openssl") is None, reason="openssl binary not available")
-@pytest.mark.parametrize("C,name", [(curves.SECP256K1, "secp256k1"), (curves.P256, "prime256v1")])
+@pytest.mark.parametrize("C,name", [(curves.SECP256K1, "secp256k1"), (curves.P256, "prime256v1"),
+                                    (curves.SM2, "SM2")])
 def test_against_openssl_explicit_params(C, name):
     o = _openssl_params(name)
     assert (o["p"], o["a"], o["b"], o["gx"], o["gy"], o["n"]) == (C.p, C.a, C.b, C.gx, C.gy, C.n)
@@ -101,3 +102,9 @@ def test_openssl_key_derivation_matches_group_law(C, cname):
     for d in [1, 2, 3, 0xDEADBEEF, C.n - 1, C.n // 3, 2**200 + 12345]:
         pub = crypto_ec.derive_private_key(d, curve).public_key().public_numbers()
         assert ec.mul(C, d, C.G) == (pub.x, pub.y), d
+
+
+def test_sm2_prime_form():
+    """The SM2 prime is the SCA-256 modulus the paper quotes (Section 4.2)."""
+    assert curves.SM2.p == 2**256 - 2**224 - 2**96 + 2**64 - 1
+    assert curves.SM2.a == curves.SM2.p - 3
