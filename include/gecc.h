@@ -195,6 +195,19 @@ int ecc_msm_bases(void* handle, size_t num_vectors, const uint32_t* scalars, uin
                   void* stream);
 int ecc_bases_destroy(void* handle);
 
+/* Window multiples for reused bases (the paper's memory-for-time trade for
+ * reused bases): stores 2^(c w) P_i for every window w of width c (W =
+ * ceil((bits(r) + 1) / c) windows, W x n points, 64 or 96 bytes each, owned by
+ * the handle and replacing an earlier table).  Afterwards every ecc_msm_bases /
+ * ecc_msm_bases_ragged call on the handle uses window width c and one shared set
+ * of 2^(c-1) buckets for all windows: no per-window reduction, no window
+ * combination.  c in 2..24, W x n < 2^31, else ECC_EINVAL; ECC_ENOMEM when the
+ * table does not fit.  Synchronous (returns after the table is built on
+ * `stream`); no call on the handle may be in flight on another stream.
+ * ecc_bases_window returns the handle's c, 0 when it has no table. */
+int ecc_bases_precompute(void* handle, int c, void* stream);
+int ecc_bases_window(void* handle);
+
 /* Ragged MSMs over resident bases (the serving form): instance i is
  * sum_j k_ij P_j over the first sizes[i] resident bases; its sizes[i] scalar
  * rows follow those of instance i - 1 in `scalars`.  sizes: HOST array of num

@@ -61,6 +61,34 @@ def time_msm_bases(curve, bases, scalars, n, vectors, torch, reps=3):
     return a.elapsed_time(b) / reps / 1e3
 
 
+def tune_precomputed(handle, vectors, scalars, torch, candidates, reps=3):
+    """Window width for a resident-bases handle with window multiples: builds
+    the table for every candidate width, times ecc_msm_bases on `vectors`
+    scalar vectors, and leaves the handle with the fastest.  Returns (c, times)
+    with times[c] = (table build s, call s)."""
+    import time
+
+    times = {}
+    for c in candidates:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ecc.ecc_bases_precompute(handle, c)
+        build = time.perf_counter() - t0
+        out = torch.empty((vectors, 24), dtype=torch.int32, device="cuda")  # 2 x 12 limbs covers every curve
+        ecc.ecc_msm_bases(handle, vectors, scalars, out)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            ecc.ecc_msm_bases(handle, vectors, scalars, out)
+        b.record()
+        torch.cuda.synchronize()
+        times[c] = (build, a.elapsed_time(b) / reps / 1e3)
+    best = min(times, key=lambda c: times[c][1])
+    ecc.ecc_bases_precompute(handle, best)
+    return best, times
+
+
 def tune(curve, log2_sizes, torch, spread=2, seed=0x6ECC7777, cache=None, vectors=1):
     """Returns {log2_n: c} and installs it in the library.  With vectors > 1
     every candidate is timed on the resident-bases form with that many scalar

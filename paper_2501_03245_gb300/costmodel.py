@@ -67,3 +67,12 @@ def msm_modmul(n_points, windows, c, buckets_touched=None):
     buckets = windows * (1 << (c - 1)) if buckets_touched is None else buckets_touched
     return (n_points * windows * BATCH_PADD_MODMUL + 2 * buckets * BATCH_PADD_MODMUL
             + windows * (c * BATCH_PDBL_MODMUL + BATCH_PADD_MODMUL))
+
+
+def msm_modmul_precomputed(n_points, windows, c):
+    """The same MSM over bases that carry their window multiples 2^(c w) P_i:
+    one batched PADD per (point, window) digit into a single set of 2^(c-1)
+    buckets, whose reduction takes two additions per bucket; no window
+    combination.  The table itself (c doublings per base and window) is built
+    once per set of bases and not counted per call."""
+    return n_points * windows * BATCH_PADD_MODMUL + 2 * (1 << (c - 1)) * BATCH_PADD_MODMUL

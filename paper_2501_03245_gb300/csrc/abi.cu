@@ -422,6 +422,23 @@ int ecc_msm_bases_ragged(void* handle, size_t num, const uint64_t* sizes, const 
   });
 }
 
+int ecc_bases_precompute(void* handle, int c, void* stream) {
+  const char* name = "ecc_bases_precompute";
+  if (!handle) return fail(ECC_EINVAL, "%s: NULL handle", name);
+  if (c < 2 || c > 24) return fail(ECC_EINVAL, "%s: window width %d outside 2..24", name, c);
+  cudaError_t e = bases_precompute(handle, c, static_cast<cudaStream_t>(stream));
+  if (e == cudaErrorInvalidValue)
+    return fail(ECC_EINVAL, "%s: windows x bases must stay below 2^31 points", name);
+  if (e == cudaErrorMemoryAllocation) return fail(ECC_ENOMEM, "%s: out of device memory", name);
+  if (e != cudaSuccess) return cuda_fail(e, name);
+  return ok();
+}
+
+int ecc_bases_window(void* handle) {
+  if (!handle) return fail(ECC_EINVAL, "ecc_bases_window: NULL handle");
+  return bases_window(handle);
+}
+
 int ecc_bases_destroy(void* handle) {
   if (!handle) return fail(ECC_EINVAL, "ecc_bases_destroy: NULL handle");
   cudaError_t e = bases_destroy(handle);

@@ -75,6 +75,8 @@ cudaError_t launch_msm(int curve, uint32_t num, const uint64_t* offsets, const u
 cudaError_t bases_create(int curve, uint64_t n, const uint32_t* points, void** handle,
                          cudaStream_t st);
 cudaError_t bases_destroy(void* handle);
+cudaError_t bases_precompute(void* handle, int c, cudaStream_t st);
+int bases_window(void* handle);
 int bases_curve(void* handle);
 uint64_t bases_count(void* handle);
 cudaError_t launch_msm_bases(void* handle, uint32_t num_vectors, const uint64_t* sizes,

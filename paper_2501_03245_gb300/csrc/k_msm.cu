@@ -21,6 +21,8 @@ cudaError_t msm_bases_bls12_381(void* bases, uint32_t num_vectors, const uint64_
                                 uint32_t* out, cudaStream_t st);
 cudaError_t points_to_mont(int curve, const uint32_t* in, uint64_t n, uint32_t* out,
                            cudaStream_t st);
+cudaError_t bases_precompute_bn254(void* bases, int c, cudaStream_t st);
+cudaError_t bases_precompute_bls12_381(void* bases, int c, cudaStream_t st);
 
 namespace {
 
@@ -105,8 +107,22 @@ uint64_t bases_count(void* handle) { return static_cast<msm_detail::Bases*>(hand
 cudaError_t bases_destroy(void* handle) {
   auto* b = static_cast<msm_detail::Bases*>(handle);
   cudaError_t e = cudaFree(b->mont);
+  if (b->pre) {
+    const cudaError_t e2 = cudaFree(b->pre);
+    if (e == cudaSuccess) e = e2;
+  }
   delete b;
   return e;
+}
+
+int bases_window(void* handle) { return static_cast<msm_detail::Bases*>(handle)->pre_c; }
+
+cudaError_t bases_precompute(void* handle, int c, cudaStream_t st) {
+  switch (bases_curve(handle)) {
+    case 2: return bases_precompute_bn254(handle, c, st);
+    case 3: return bases_precompute_bls12_381(handle, c, st);
+  }
+  return cudaErrorNotSupported;
 }
 
 cudaError_t launch_msm_bases(void* handle, uint32_t num_vectors, const uint64_t* sizes,

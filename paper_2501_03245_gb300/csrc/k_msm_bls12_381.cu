@@ -22,4 +22,8 @@ cudaError_t points_to_mont_bls12_381(const uint32_t* in, uint64_t n, uint32_t* o
   return cudaGetLastError();
 }
 
+cudaError_t bases_precompute_bls12_381(void* bases, int c, cudaStream_t st) {
+  return msm_detail::precompute_t<BLS12_381>(static_cast<msm_detail::Bases*>(bases), c, st);
+}
+
 }  // namespace ecc

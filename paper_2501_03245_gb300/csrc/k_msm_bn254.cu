@@ -29,4 +29,8 @@ cudaError_t points_to_mont(int curve, const uint32_t* in, uint64_t n, uint32_t* 
   return points_to_mont_bls12_381(in, n, out, st);
 }
 
+cudaError_t bases_precompute_bn254(void* bases, int c, cudaStream_t st) {
+  return msm_detail::precompute_t<BN254>(static_cast<msm_detail::Bases*>(bases), c, st);
+}
+
 }  // namespace ecc

@@ -31,10 +31,17 @@ constexpr int kAccChunk = 32;       // entries per running-sum chunk (rounds of 
 struct MsmInst {
   uint32_t n;            // points of the instance
   uint32_t c;            // window bits
-  uint32_t W;            // windows
+  uint32_t W;            // windows (digits per scalar)
   uint32_t bucket_base;  // first global bucket id
   uint64_t point_off;    // first point in the global bases array
   uint64_t scalar_off;   // first scalar in the global scalar array
+  // Bases with precomputed window multiples: window w of point i is the point
+  // 2^(c w) P_i at index w * pre_stride + i, all windows share one set of
+  // buckets (Wr = 1) and need no combination.  pre_stride = 0: Wr = W rows of
+  // buckets, one per window.
+  uint64_t pre_stride;
+  uint32_t Wr;           // bucket rows (windows reduced separately)
+  uint32_t pad;
 };
 
 // ------------------------------------------------------------------ digits
@@ -105,8 +112,9 @@ __global__ void k_msm_count(const MsmInst* inst, int num, const uint32_t* __rest
   for (int q = 0; q < 8; ++q) k[q] = scalars[8 * g + q];
   scalar_mod_r<C>(k);
   const uint32_t half = 1u << (in.c - 1);
+  const uint32_t row = in.pre_stride ? 0u : half;
   for_each_digit(k, in.c, in.W, [&](int w, int d) {
-    const uint32_t b = in.bucket_base + w * half + (uint32_t)(d < 0 ? -d : d) - 1;
+    const uint32_t b = in.bucket_base + w * row + (uint32_t)(d < 0 ? -d : d) - 1;
     atomicAdd(count + b, 1u);
   });
 }
@@ -125,11 +133,13 @@ __global__ void k_msm_scatter(const MsmInst* inst, int num, const uint32_t* __re
   for (int q = 0; q < 8; ++q) k[q] = scalars[8 * g + q];
   scalar_mod_r<C>(k);
   const uint32_t half = 1u << (in.c - 1);
-  const uint32_t pidx = (uint32_t)(in.point_off + (g - in.scalar_off));
+  const uint32_t row = in.pre_stride ? 0u : half;
+  const uint64_t pidx = in.point_off + (g - in.scalar_off);
   for_each_digit(k, in.c, in.W, [&](int w, int d) {
-    const uint32_t b = in.bucket_base + w * half + (uint32_t)(d < 0 ? -d : d) - 1;
+    const uint32_t b = in.bucket_base + w * row + (uint32_t)(d < 0 ? -d : d) - 1;
     const uint32_t p = atomicAdd(cursor + b, 1u);
-    vals[(uint64_t)(p % kAccChunk) * n_chunks + p / kAccChunk] = pidx | (d < 0 ? 0x80000000u : 0u);
+    const uint32_t idx = (uint32_t)(pidx + (uint64_t)w * in.pre_stride);  // < 2^31 (host check)
+    vals[(uint64_t)(p % kAccChunk) * n_chunks + p / kAccChunk] = idx | (d < 0 ? 0x80000000u : 0u);
   });
 }
 
@@ -718,7 +728,7 @@ __global__ void k_msm_combine(const MsmInst* inst, const uint64_t* fin, uint32_t
   constexpr int N = F::N;
   const uint32_t id = blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= num) return;
-  const uint32_t c = inst[id].c, W = inst[id].W;
+  const uint32_t c = inst[id].c, W = inst[id].Wr;
   const Jac<F>* Sw = S + fin[id];
   Jac<F> acc = Sw[W - 1];
   for (int w = (int)W - 2; w >= 0; --w) {
@@ -756,6 +766,88 @@ __global__ void k_points_to_mont(const uint32_t* __restrict__ in, uint64_t n, ui
   for (int q = 0; q < N; ++q) {
     out[2 * N * i + q] = x[q];
     out[2 * N * i + N + q] = y[q];
+  }
+}
+
+// ------------------------------------------------------------------ window multiples
+// For bases reused across calls: window w of base i becomes 2^(c w) P_i
+// (window-major AoS, Montgomery form), so one set of buckets serves every
+// window.  Window w is window w-1 doubled c times: c batched PDBL rounds per
+// window, every item an independent base.
+template <class C>
+struct ShiftArgs {
+  using F = typename C::Fp;
+  uint32_t* pre;     // W windows of n points, 2N words each; window 0 filled in
+  uint64_t n;
+  uint32_t W, c;
+  SoA<F> M;
+  uint64_t per_cta;
+};
+
+template <class C>
+ECC_DEV void aos_load(const uint32_t* base, uint64_t i, uint32_t* x, uint32_t* y) {
+  constexpr int N = C::Fp::N;
+  const uint4* p = reinterpret_cast<const uint4*>(base + i * 2 * N);
+#pragma unroll
+  for (int g = 0; g < N / 4; ++g) {
+    const uint4 t = p[g];
+    x[4 * g] = t.x; x[4 * g + 1] = t.y; x[4 * g + 2] = t.z; x[4 * g + 3] = t.w;
+  }
+#pragma unroll
+  for (int g = 0; g < N / 4; ++g) {
+    const uint4 t = p[N / 4 + g];
+    y[4 * g] = t.x; y[4 * g + 1] = t.y; y[4 * g + 2] = t.z; y[4 * g + 3] = t.w;
+  }
+}
+
+template <class C>
+ECC_DEV void aos_store(uint32_t* base, uint64_t i, const uint32_t* x, const uint32_t* y) {
+  constexpr int N = C::Fp::N;
+  uint4* p = reinterpret_cast<uint4*>(base + i * 2 * N);
+#pragma unroll
+  for (int g = 0; g < N / 4; ++g) p[g] = make_uint4(x[4 * g], x[4 * g + 1], x[4 * g + 2], x[4 * g + 3]);
+#pragma unroll
+  for (int g = 0; g < N / 4; ++g)
+    p[N / 4 + g] = make_uint4(y[4 * g], y[4 * g + 1], y[4 * g + 2], y[4 * g + 3]);
+}
+
+template <class C>
+struct ShiftRound {
+  using F = typename C::Fp;
+  static constexpr int N = F::N;
+  static constexpr int OPS = 1;
+  const uint32_t* src;
+  uint32_t* dst;
+  bool live;
+  ECC_DEV void den_c(size_t i, int, uint32_t* d) {
+    uint32_t x[N], y[N];
+    aos_load<C>(src, i, x, y);
+    live = dbl_den<C>(d, y);
+  }
+  ECC_DEV void den_d(size_t i, int j, uint32_t* d) { den_c(i, j, d); }
+  ECC_DEV void finish(size_t i, const uint32_t (*inv)[N]) {
+    uint32_t x[N], y[N];
+    aos_load<C>(src, i, x, y);
+    dbl_finish<C>(x, y, live, inv[0], x, y);
+    aos_store<C>(dst, i, x, y);
+  }
+};
+
+template <class C, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, kGasResidentThreads / BLOCK) k_bases_shift(ShiftArgs<C> a) {
+  using F = typename C::Fp;
+  constexpr int N = F::N;
+  auto& sm = gas_smem<N, BLOCK>();
+  const uint64_t begin = blockIdx.x * a.per_cta;
+  uint64_t end = begin + a.per_cta;
+  if (end > a.n) end = a.n;
+  if (end < begin) end = begin;
+  for (uint32_t w = 1; w < a.W; ++w) {
+    uint32_t* dst = a.pre + (uint64_t)w * a.n * 2 * N;
+    for (uint32_t r = 0; r < a.c; ++r) {
+      ShiftRound<C> rd{r == 0 ? dst - a.n * 2 * N : dst, dst};
+      batch_round<F, BLOCK>(rd, begin, end, a.M, sm);
+    }
   }
 }
 

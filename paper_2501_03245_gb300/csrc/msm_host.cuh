@@ -127,16 +127,17 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
   // ---- 4: bucket reduction.  Instances are grouped by window width (same
   // level structure); the items of every level are laid out group-major so a
   // level of all groups is one launch.
-  std::map<uint32_t, std::vector<uint32_t>> groups;
-  for (int i = 0; i < num; ++i) groups[L.inst[i].c].push_back((uint32_t)i);
+  // groups by (window width, bucket rows per instance)
+  std::map<std::pair<uint32_t, uint32_t>, std::vector<uint32_t>> groups;
+  for (int i = 0; i < num; ++i) groups[{L.inst[i].c, L.inst[i].Wr}].push_back((uint32_t)i);
   std::vector<std::vector<uint32_t>> elems;  // per group: elements per row, by level
   std::vector<uint64_t> rows;
   for (auto& g : groups) {
-    std::vector<uint32_t> el{1u << (g.first - 1)};
+    std::vector<uint32_t> el{1u << (g.first.first - 1)};
     el.push_back((el[0] + kRedChunk1 - 1) / kRedChunk1);
     while (el.back() > 1) el.push_back((el.back() + kRedChunkN - 1) / kRedChunkN);
     elems.push_back(el);
-    rows.push_back((uint64_t)g.second.size() * L.inst[g.second[0]].W);
+    rows.push_back((uint64_t)g.second.size() * g.first.second);
   }
   const size_t n_groups = elems.size();
   size_t levels = 0;
@@ -161,8 +162,8 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
       for (size_t ii = 0; ii < grp.second.size(); ++ii) {
         const uint32_t id = grp.second[ii];
         ranges.push_back(RedRange{t, id, elems[g][1]});
-        t += (uint64_t)L.inst[id].W * elems[g][1];
-        fin[id] = lvl_off[last][g] + (uint64_t)ii * L.inst[id].W;
+        t += (uint64_t)L.inst[id].Wr * elems[g][1];
+        fin[id] = lvl_off[last][g] + (uint64_t)ii * L.inst[id].Wr;
       }
       ++g;
     }
@@ -251,19 +252,24 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
   return cudaSuccess;
 }
 
+// pre_c > 0: the bases hold precomputed window multiples for width pre_c,
+// pre_stride points apart.
 inline Layout plan(int curve, uint32_t num, const uint64_t* sizes, const uint64_t* point_off,
-            const uint64_t* scalar_off, const int* cs) {
+            const uint64_t* scalar_off, const int* cs, int pre_c = 0, uint64_t pre_stride = 0) {
   Layout L;
   L.inst.resize(num);
   for (uint32_t i = 0; i < num; ++i) {
     MsmInst& m = L.inst[i];
     m.n = (uint32_t)sizes[i];
-    m.c = (uint32_t)(cs && cs[i] > 0 ? cs[i] : msm_window(curve, sizes[i]));
+    m.c = (uint32_t)(pre_c > 0 ? pre_c : cs && cs[i] > 0 ? cs[i] : msm_window(curve, sizes[i]));
     m.W = (uint32_t)windows_for(curve, (int)m.c);
     m.bucket_base = (uint32_t)L.buckets;
     m.point_off = point_off[i];
     m.scalar_off = scalar_off[i];
-    L.buckets += (uint64_t)m.W << (m.c - 1);
+    m.pre_stride = pre_c > 0 ? pre_stride : 0;
+    m.Wr = pre_c > 0 ? 1u : m.W;
+    m.pad = 0;
+    L.buckets += (uint64_t)m.Wr << (m.c - 1);
     L.entries_max += (uint64_t)m.W * m.n;
     L.total_points += m.n;
   }
@@ -297,8 +303,57 @@ cudaError_t msm_points(int curve, uint32_t num, const uint64_t* offsets, const u
 struct Bases {
   int curve;
   uint64_t n;
-  uint32_t* mont;  // AoS Montgomery affine, owned
+  uint32_t* mont;          // AoS Montgomery affine, owned
+  uint32_t* pre = nullptr; // window multiples (window-major, window 0 = mont copy), owned
+  int pre_c = 0;           // window width of pre (0: none)
 };
+
+// Fills bs->pre with 2^(c w) P_i for w < W (W windows of width c).
+template <class C>
+cudaError_t precompute_t(Bases* bs, int c, cudaStream_t st) {
+  using F = typename C::Fp;
+  constexpr int N = F::N;
+  const uint32_t W = (uint32_t)windows_for(bs->curve, c);
+  const uint64_t n = bs->n;
+  if ((uint64_t)W * n >= (1ull << 31)) return cudaErrorInvalidValue;  // 31-bit point indices
+  uint32_t* pre = nullptr;
+  cudaError_t e = cudaMalloc(&pre, std::max<uint64_t>(W * n, 1) * 2 * N * 4);
+  if (e != cudaSuccess) return e;
+  if (n) e = cudaMemcpyAsync(pre, bs->mont, n * 2 * N * 4, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess && n && W > 1) {
+    Scratch m;
+    e = m.alloc(soa_bytes<F>(n), st);
+    if (e == cudaSuccess) {
+      ShiftArgs<C> a;
+      a.pre = pre;
+      a.n = n;
+      a.W = W;
+      a.c = (uint32_t)c;
+      a.M = SoA<F>{m.as<uint4>(), n};
+      uint64_t ctas = (uint64_t)device_sm_count() * kGasCtasPerSm;
+      uint64_t per = (n + ctas - 1) / ctas;
+      if (per < 32) per = 32;
+      ctas = (n + per - 1) / per;
+      a.per_cta = per;
+      const size_t smem = sizeof(GasSmem<N, kAccBlock>);
+      e = cudaFuncSetAttribute(k_bases_shift<C, kAccBlock>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) {
+        k_bases_shift<C, kAccBlock><<<(unsigned)ctas, kAccBlock, smem, st>>>(a);
+        e = cudaGetLastError();
+      }
+    }
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the old table may be in use until here
+  if (e != cudaSuccess) {
+    cudaFree(pre);
+    return e;
+  }
+  if (bs->pre) cudaFree(bs->pre);
+  bs->pre = pre;
+  bs->pre_c = c;
+  return cudaSuccess;
+}
 
 template <class C>
 cudaError_t msm_bases_t(Bases* bs, uint32_t num_vectors, const uint64_t* vec_sizes,
@@ -312,8 +367,9 @@ cudaError_t msm_bases_t(Bases* bs, uint32_t num_vectors, const uint64_t* vec_siz
     soff[v] = acc;
     acc += sizes[v];
   }
-  Layout L = plan(bs->curve, num_vectors, sizes.data(), poff.data(), soff.data(), nullptr);
-  return run_set<C>(bs->curve, L, bs->mont, scalars, out, st);
+  Layout L = plan(bs->curve, num_vectors, sizes.data(), poff.data(), soff.data(), nullptr,
+                  bs->pre ? bs->pre_c : 0, bs->n);
+  return run_set<C>(bs->curve, L, bs->pre ? bs->pre : bs->mont, scalars, out, st);
 }
 
 }  // namespace msm_detail

@@ -56,6 +56,8 @@ _SIGS = {
     "ecc_bench_imad": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "ecc_bench_inv": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_size_t, ctypes.c_int,
                                      ctypes.c_void_p, ctypes.c_void_p]),
+    "ecc_bases_precompute": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "ecc_bases_window": (ctypes.c_int, [ctypes.c_void_p]),
     "ecc_bench_modmul": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p,
                                         ctypes.c_void_p]),
 }
@@ -216,6 +218,17 @@ def ecc_msm_bases_ragged(handle, num, sizes, scalars, out, stream=None):
 
 def ecc_bases_destroy(handle):
     return _check(load().ecc_bases_destroy(handle))
+
+
+def ecc_bases_precompute(handle, c, stream=None):
+    return _check(load().ecc_bases_precompute(handle, c, _stream(stream)))
+
+
+def ecc_bases_window(handle):
+    rc = load().ecc_bases_window(handle)
+    if rc < 0:
+        _check(rc)
+    return rc
 
 
 def ecc_msm_window(curve, n):

@@ -33,3 +33,12 @@ def test_verify_count_structure():
     assert m == 260 * 7 + 101 * 6 + 7 + 9
     assert costmodel.verify_imad() == m * 136
     assert costmodel.fpmul_modmul() == 32 * 6
+
+
+def test_msm_precomputed_count():
+    # one bucket set instead of W, no window combination
+    n, c = 1 << 20, 16
+    W = -(-256 // c)
+    assert costmodel.msm_modmul_precomputed(n, W, c) == 6 * n * W + 2 * 6 * (1 << (c - 1))
+    assert costmodel.msm_modmul(n, W, c) - costmodel.msm_modmul_precomputed(n, W, c) == \
+        2 * 6 * (W - 1) * (1 << (c - 1)) + W * (7 * c + 6)

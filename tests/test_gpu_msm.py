@@ -157,3 +157,58 @@ def test_msm_heavy_buckets(gpu_lib, cid, n, c, same):
     finally:
         if c:
             gpu_lib.ecc_msm_set_window(cid, log2n, 0)
+
+
+@pytest.mark.parametrize("cid,c", [(2, 7), (2, 13), (3, 5), (3, 12)])
+def test_msm_bases_precomputed_windows(gpu_lib, cid, c):
+    """Resident bases with window multiples 2^(c w) P_i: every vector against the
+    oracle and against the same handle without the table, the ragged form too."""
+    import torch
+
+    C = curves.BY_ID[cid]
+    n, V = 700, 3
+    pts, _ = random_points(C, n, 0x6ECC1500 + cid)
+    _, ks = synth.msm_raw(0x6ECC1600 + cid + c, n, C.n, V)
+    ks[1][:50] = ks[1][50:100]          # repeated digits: buckets with many entries
+    ks[2][0] = synth.ints_to_limbs([C.n - 1], 8)[0]
+    pts_l = _pts_limbs(C, pts)
+    h = gpu_lib.ecc_bases_create(cid, n, to_cuda(pts_l))
+    try:
+        k_all = to_cuda(np.concatenate(ks, axis=0))
+        plain = torch.zeros((V, 2 * C.limbs), dtype=torch.int32, device="cuda")
+        gpu_lib.ecc_msm_bases(h, V, k_all, plain)
+        assert gpu_lib.ecc_bases_window(h) == 0
+        gpu_lib.ecc_bases_precompute(h, c)
+        assert gpu_lib.ecc_bases_window(h) == c
+        out = torch.zeros_like(plain)
+        gpu_lib.ecc_msm_bases(h, V, k_all, out)
+        sizes = np.array([n, 1, 333], np.uint64)
+        rk = np.concatenate([ks[0], ks[1][:1], ks[2][:333]], axis=0)
+        rout = torch.zeros((3, 2 * C.limbs), dtype=torch.int32, device="cuda")
+        gpu_lib.ecc_msm_bases_ragged(h, 3, sizes, to_cuda(rk), rout)
+        torch.cuda.synchronize()
+        got = limbs_to_points(C, from_cuda(out).view(np.uint32))
+        assert got == limbs_to_points(C, from_cuda(plain).view(np.uint32))
+        for v in range(V):
+            assert got[v] == _oracle_msm(cid, pts_l, ks[v]), v
+        rgot = limbs_to_points(C, from_cuda(rout).view(np.uint32))
+        assert rgot[0] == got[0]
+        assert rgot[1] == _oracle_msm(cid, pts_l[:1], ks[1][:1])
+        assert rgot[2] == _oracle_msm(cid, pts_l[:333], ks[2][:333])
+    finally:
+        gpu_lib.ecc_bases_destroy(h)
+
+
+def test_msm_bases_precompute_rejects(gpu_lib):
+    from paper_2501_03245_gb300 import ecc
+
+    C = curves.BN254
+    pts, _ = random_points(C, 8, 0x6ECC1700)
+    h = gpu_lib.ecc_bases_create(2, 8, to_cuda(_pts_limbs(C, pts)))
+    try:
+        for c in (1, 25):
+            with pytest.raises(ecc.EccError):
+                gpu_lib.ecc_bases_precompute(h, c)
+        assert gpu_lib.ecc_bases_window(h) == 0
+    finally:
+        gpu_lib.ecc_bases_destroy(h)
