@@ -3,7 +3,8 @@
 Requests of two kinds arrive over time: verification of a batch of secp256k1
 triples, and a BN254 MSM of n points over device-resident bases (the same
 bases for every request; a request uses the first n of them with its own
-scalars).  The server keeps one CUDA stream per kind.  Whenever a kind's
+scalars).  The resident bases carry their window multiples (one bucket set per
+MSM, width --table-c).  The server keeps one CUDA stream per kind.  Whenever a kind's
 previous round has finished on the device and requests of that kind are
 waiting, it forms the next round from the waiting requests in arrival order --
 as many as fit the round limits and the free part of the device-memory budget
@@ -15,7 +16,7 @@ is running join the next one.  Completion times are read from CUDA events
 completion minus arrival.
 
 Run as a module for the load sweep:
-  python -m paper_2501_03245_gb300.serving --loads 0.1,0.3,0.5,0.7,0.9 --requests 300
+  python -m paper_2501_03245_gb300.serving --loads 0.1,0.3,0.5,0.7,0.9 --requests 2000
 """
 import argparse
 import collections
@@ -73,7 +74,7 @@ def make_trace(seed, count, rate, mix=0.5, verify_max_log2=12, msm_lo_log2=12, m
 class Server:
     def __init__(self, torch, pool_triples=1 << 16, n_bases=1 << 20, pool_scalars=1 << 22,
                  hbm_budget=8 << 30, max_verify_round=1 << 18, max_msm_round_points=1 << 22,
-                 seed=synth.SEED_BASE + 4):
+                 seed=synth.SEED_BASE + 4, table_c=16):
         self.torch = torch
         self.budget = hbm_budget
         self.max_verify_round = max_verify_round
@@ -97,6 +98,9 @@ class Server:
         self.bases_pts = torch.empty((n_bases, 16), dtype=torch.int32, device=dev)
         ecc.ecc_fixed_base_mul(ecc.ECC_BN254, n_bases, to(a.view(np.int32)), self.bases_pts)
         self.bases = ecc.ecc_bases_create(ecc.ECC_BN254, n_bases, self.bases_pts)
+        if table_c:
+            # resident window multiples: every MSM round uses one bucket set
+            ecc.ecc_bases_precompute(self.bases, table_c)
         self.n_bases = n_bases
         ks = synth.uniform_limbs(seed, synth.S_SCALAR, pool_scalars, BN254_R)
         self.scalars = to(ks.view(np.int32))
@@ -236,10 +240,12 @@ def main():
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--loads", default="0.1,0.3,0.5,0.7,0.9")
-    ap.add_argument("--requests", type=int, default=300)
+    ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--seed", type=int, default=synth.SEED_BASE + 4)
+    ap.add_argument("--table-c", type=int, default=16,
+                    help="window width of the resident bases' window multiples (0: none)")
     args = ap.parse_args()
-    srv = Server(torch, seed=args.seed)
+    srv = Server(torch, seed=args.seed, table_c=args.table_c)
     try:
         # peak: the whole trace offered at once (saturation)
         sat = make_trace(args.seed, args.requests, float("inf"))
