@@ -40,7 +40,13 @@ ECC_DEV int ctz64(uint64_t x) {
 
 // 62 divsteps on the low bits of f and g (f odd).  delta is carried across calls.
 // A run of k divsteps with g even (g <- g/2, delta <- delta + 1) is applied at
-// once by counting trailing zeros; only odd-g steps go one at a time.
+// once by counting trailing zeros.  With g odd and delta > 0 the divstep swaps
+// and goes alone.  With g odd and delta <= 0, the next k <= 1 - delta divsteps
+// cannot swap: each adds f when g is odd and halves, so together they add w f
+// with w = -g / f mod 2^k (the unique multiple that clears k low bits) and
+// halve k times; the addition is done here (k <= 6, f^-1 mod 64 by one Newton
+// step from f, which is its own inverse mod 8) and the halvings by the next
+// trailing-zero count.
 ECC_DEV Trans divsteps62(int64_t& delta, uint64_t f, uint64_t g) {
   int64_t u = 1, v = 0, q = 0, r = 1;
   int left = 62;
@@ -53,8 +59,7 @@ ECC_DEV Trans divsteps62(int64_t& delta, uint64_t f, uint64_t g) {
     delta += z;
     left -= z;
     if (left == 0) break;
-    // g odd: one divstep
-    if (delta > 0) {
+    if (delta > 0) {  // g odd: one swapping divstep
       delta = 1 - delta;
       const uint64_t nf = g;
       g = (g - f) >> 1;
@@ -64,15 +69,17 @@ ECC_DEV Trans divsteps62(int64_t& delta, uint64_t f, uint64_t g) {
       r = r - v;
       u = nu;
       v = nv;
-    } else {
-      delta = 1 + delta;
-      g = (g + f) >> 1;
-      q = q + u;
-      r = r + v;
-      u = 2 * u;
-      v = 2 * v;
+      if (--left == 0) break;
+    } else {  // g odd, delta <= 0: k non-swapping divsteps at once
+      int k = 1 - delta < (int64_t)left ? (int)(1 - delta) : left;
+      if (k > 6) k = 6;
+      const uint32_t fl = (uint32_t)f;
+      const uint32_t finv = fl * (2u - fl * fl);  // f^-1 mod 64
+      const uint64_t w = (0u - (uint32_t)g * finv) & ((1u << k) - 1u);
+      g += w * f;
+      q += (int64_t)w * u;
+      r += (int64_t)w * v;
     }
-    if (--left == 0) break;
   }
   return Trans{u, v, q, r};
 }
