@@ -51,6 +51,25 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x):
+    """The largest of every rank's x (x itself when not distributed).  The
+    tensor lives where the process group's backend expects it."""
+    import torch
+
+    if not (torch.distributed.is_available() and torch.distributed.is_initialized()):
+        return float(x)
+    dev = "cuda" if torch.distributed.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, seconds, world):
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (weak scaling: every rank does the same units)."""
+    return units_per_rank * world / max_over_ranks(seconds)
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -215,7 +234,7 @@ def _event_time(torch, fn, reps):
     return a.elapsed_time(b) / 1e3 / reps
 
 
-def bench_msm(ecc, costmodel, synth, torch, peak, rank, n=1 << 20, V=16):
+def bench_msm(ecc, costmodel, synth, torch, peak, rank, n=1 << 20, V=16, world=1):
     """BLS12-381 MSM: n resident bases a_i G (2^20 by default), V scalar vectors
     per step (16 by default; one ecc_msm_bases call), against the plain form (one
     MSM launch sequence per vector).  The bases are reused across calls, so they
@@ -255,15 +274,15 @@ def bench_msm(ecc, costmodel, synth, torch, peak, rank, n=1 << 20, V=16):
     alg_tab = costmodel.msm_modmul(n, W_tab, c_tab) * V * costmodel.imad_per_modmul(12)
     shape = f"2^{log2n}" if n & (n - 1) == 0 else str(n)
     return {"workload": f"MSM BLS12-381 G1, {shape} resident bases, {V} scalar vectors per step",
-            "value": n * V / t, "unit": "points/s", "ms_per_step": t * 1e3, "window_c": c,
+            "value": job_rate(n * V, t, world), "unit": "points/s", "ms_per_step": t * 1e3, "window_c": c,
             "form": "resident bases with window multiples 2^(c w) P_i, one bucket set",
             "table": {"build_ms": sweep[c][0] * 1e3, "bytes": W * n * 96,
                       "sweep_ms": {str(k): round(v[1] * 1e3, 2) for k, v in sweep.items()}},
             "bit_equal_to_no_table": same,
-            "no_table": {"value": n * V / t_tab, "ms_per_step": t_tab * 1e3, "window_c": c_tab,
+            "no_table": {"value": job_rate(n * V, t_tab, world), "ms_per_step": t_tab * 1e3, "window_c": c_tab,
                          "autotuned": {str(k): v for k, v in tuned.items()},
                          "frac": alg_tab / t_tab / peak},
-            "plain": {"value": n * V / t1, "unit": "points/s",
+            "plain": {"value": job_rate(n * V, t1, world), "unit": "points/s",
                       "form": "one MSM launch sequence per scalar vector (same table)"},
             "roofline": {"bound": "alu", "achieved": alg / t / 1e12, "peak": peak / 1e12,
                          "unit": "T IMAD.WIDE/s", "frac": alg / t / peak,
@@ -277,7 +296,7 @@ def bench_msm(ecc, costmodel, synth, torch, peak, rank, n=1 << 20, V=16):
 PAPER_SM2_VERIFY_A100 = 4372853.0
 
 
-def bench_sm2(ecc, synth, torch, rank, n, steps):
+def bench_sm2(ecc, synth, torch, rank, n, steps, world=1):
     """ECDSA verification on the SM2 curve, the paper's curve: 2^20 triples with
     the same recipe as the P-256 line (1/16 corrupted), inputs resident."""
     curve = ecc.ECC_SM2
@@ -286,14 +305,15 @@ def bench_sm2(ecc, synth, torch, rank, n, steps):
     for _ in range(3):
         ecc.ecc_verify_batch(curve, n, e, r, s, pub, ok)
     t = _event_time(torch, lambda: ecc.ecc_verify_batch(curve, n, e, r, s, pub, ok), steps)
-    return {"workload": "ECDSA verify, SM2, 2^20 seeded triples, 1/16 corrupted", "value": n / t,
+    value = job_rate(n, t, world)
+    return {"workload": "ECDSA verify, SM2, 2^20 seeded triples, 1/16 corrupted", "value": value,
             "unit": "verifies/s", "ms_per_step": t * 1e3, "valid_signatures": int(ok.sum().item()),
             "paper": {"value": PAPER_SM2_VERIFY_A100, "hardware": "NVIDIA A100 40 GB",
                       "source": "Table 4"},
-            "ratio_to_paper": n / t / PAPER_SM2_VERIFY_A100}
+            "ratio_to_paper": value / world / PAPER_SM2_VERIFY_A100}
 
 
-def bench_ragged(ecc, synth, torch, rank):
+def bench_ragged(ecc, synth, torch, rank, world=1):
     """BN254 ragged batch: 256 MSMs with log-uniform sizes 2^10..2^18, all in one
     launch sequence captured once in a CUDA graph and replayed, against one
     launch sequence per MSM."""
@@ -333,11 +353,12 @@ def bench_ragged(ecc, synth, torch, rank):
                                       for i in range(256)], 1)
     best = graph if graph else eager
     return {"workload": "256 BN254 MSMs, sizes log-uniform 2^10..2^18, one launch sequence",
-            "points": total, "value": total / best, "unit": "points/s",
+            "points": total, "value": job_rate(total, best, world), "unit": "points/s",
             "graph_replay_ms": graph * 1e3 if graph else None, "eager_ms": eager * 1e3,
             "graph_bit_equal": graph_ok,
             "autotuned": {str(k): v for k, v in sorted(tuned.items())},
-            "plain": {"value": total / per, "unit": "points/s", "form": "one launch sequence per MSM"}}
+            "plain": {"value": job_rate(total, per, world), "unit": "points/s",
+                      "form": "one launch sequence per MSM"}}
 
 
 def run_reference(args):
@@ -431,11 +452,8 @@ def run_ours(args):
     clk.stop()
     total_s = t_all0.elapsed_time(t_all1) / 1e3
     per_launch = [a.elapsed_time(b) / 1e3 for a, b in events]
-    if world > 1:
-        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = n * world * args.steps / total_s
+    value = job_rate(n * args.steps, total_s, world)
+    total_s = max_over_ranks(total_s)
 
     # end to end through the C ABI with pinned host buffers (copies inside the timed region)
     e_h = e.cpu().pin_memory()
@@ -451,6 +469,7 @@ def run_ours(args):
         ecc.ecc_verify_batch(CURVE_P256, n, e_h, r_h, s_h, p_h, ok_h, stream)
     barrier()
     e2e_s = time.perf_counter() - t0
+    e2e_value = job_rate(n * e2e_steps, e2e_s, world)
     e2e_ok = bool(torch.equal(ok_h, ok.cpu()))
 
     # plain form: one verification per launch
@@ -489,18 +508,19 @@ def run_ours(args):
                      "basis": f"{costmodel.verify_modmul()} modmul x 136 wide mul-adds per verify; "
                               "peak = measured mad.lo/madc.hi pair rate (ecc_bench_imad, same run)"},
         "plain": {"value": plain, "unit": "verifies/s", "form": "one verification per launch"},
-        "e2e": {"value": n * e2e_steps / e2e_s, "unit": "verifies/s",
+        "e2e": {"value": e2e_value, "unit": "verifies/s",
                 "h2d_bytes_per_step": 160 * n, "d2h_bytes_per_step": n, "bit_equal": e2e_ok},
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
     }
     del e, r, s, pub, ok, e_h, r_h, s_h, p_h, ok_h
     if not args.no_msm:
-        line["msm"] = bench_msm(ecc, costmodel, synth, torch, peak, rank, args.msm_n, args.msm_vectors)
+        line["msm"] = bench_msm(ecc, costmodel, synth, torch, peak, rank, args.msm_n, args.msm_vectors,
+                                world)
         if not args.no_ragged:
-            line["ragged"] = bench_ragged(ecc, synth, torch, rank)
+            line["ragged"] = bench_ragged(ecc, synth, torch, rank, world)
     if not args.no_sm2:
-        line["sm2"] = bench_sm2(ecc, synth, torch, rank, n, args.steps)
+        line["sm2"] = bench_sm2(ecc, synth, torch, rank, n, args.steps, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline
     if rank == 0:

@@ -76,3 +76,31 @@ def test_verify_host_buffers(gpu_lib):
 def test_verify_tiny_batches(gpu_lib, n):
     e, r, s, pub = make_triples(1, n, 0x6ECC0700 + n, 0)
     assert run_gpu(gpu_lib, 1, e, r, s, pub).sum() == n
+
+
+def test_verify_ragged_sets_in_a_cuda_graph(gpu_lib):
+    """Verification requests of uneven sizes concatenated into one call,
+    captured once in a CUDA graph and replayed on new inputs in the same
+    buffers: every replay bit-exact against the oracle."""
+    import torch
+
+    cid = 4
+    sizes = [1, 17, 300, 2048, 64, 5]
+    n = sum(sizes)
+    sets = [make_triples(cid, n, 0x6ECC1800 + k, 8) for k in range(2)]
+    bufs = [torch.zeros(x.shape, dtype=torch.uint8, device="cuda") for x in sets[0]]
+    ok = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    for b, x in zip(bufs, sets[0]):
+        b.copy_(torch.from_numpy(x))
+    gpu_lib.ecc_verify_batch(cid, n, *bufs, ok)  # builds the fixed-base table outside the capture
+    torch.cuda.synchronize()
+    st = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st):
+        gpu_lib.ecc_verify_batch(cid, n, *bufs, ok, st)
+    for x in sets:
+        for b, arr in zip(bufs, x):
+            b.copy_(torch.from_numpy(arr))
+        g.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(from_cuda(ok), cpp_oracle.verify(cid, *x))
