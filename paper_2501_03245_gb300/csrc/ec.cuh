@@ -292,9 +292,7 @@ __device__ void cta_invert(uint32_t* out, const uint32_t* in, GasSmem<F::N, BLOC
     mont_mul<F>(v, v, t);
   }
   fe_copy<F>(out, v);
-  // No closing barrier: a thread reads back only its own tree column, and
-  // warp_tot / warp_inv are written again only after the next call's first
-  // barrier, which no warp reaches before it has finished reading them here.
+  __syncthreads();  // shared storage is reused by the next round
 }
 
 // --------------------------------------------------------------------------
