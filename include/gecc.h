@@ -172,7 +172,9 @@ int ecc_sign_batch(ecc_curve_t curve, size_t n, const uint8_t* d, const uint8_t*
  * assumed in the prime-order subgroup); scalars: n x 8 limbs, any 256-bit value
  * (reduced mod the group order r).  out: one affine point (2 * ecc_limbs()
  * limbs), (0, 0) when the sum is O.  The window width follows the size class
- * (ecc_msm_window). */
+ * (ecc_msm_window).  Sizes: at most 2^28 points per call, and fewer than 2^31
+ * (point, window) digits and 2^31 buckets over all instances of one call (the
+ * sort and the reduction index with 32-bit words), else ECC_EINVAL. */
 int ecc_msm(ecc_curve_t curve, size_t n, const uint32_t* points, const uint32_t* scalars,
             uint32_t* out, void* stream);
 

@@ -321,6 +321,15 @@ int ecc_msm_ragged(ecc_curve_t curve, size_t num, const uint64_t* offsets, const
   if (rows && (!points || !scalars)) return fail(ECC_EINVAL, "%s: NULL pointer", name);
   if ((points && !aligned4(points)) || (scalars && !aligned4(scalars)) || !aligned4(out))
     return fail(ECC_EINVAL, "%s: pointers must be 4-byte aligned", name);
+  {
+    std::vector<uint64_t> sz(num);
+    for (size_t i = 0; i < num; ++i) sz[i] = offsets[i + 1] - offsets[i];
+    uint64_t digits = 0, buckets = 0;
+    msm_counts(curve, num, sz.data(), 0, 0, &digits, &buckets);
+    if (digits >= kMsmMaxDigits || buckets >= kMsmMaxDigits)
+      return fail(ECC_EINVAL, "%s: the batch needs 2^31 or more (point, window) digits or buckets; "
+                  "split it", name);
+  }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int L = field_limbs(curve, 0);
   const uint32_t* pb = points ? points + offsets[0] * 2 * L : points;
@@ -383,6 +392,11 @@ int ecc_msm_bases(void* handle, size_t num_vectors, const uint32_t* scalars, uin
   if (num_vectors > 4096) return fail(ECC_EINVAL, "%s: num_vectors > 4096", name);
   const int curve = bases_curve(handle);
   const uint64_t n = bases_count(handle);
+  uint64_t digits = 0, buckets = 0;
+  msm_counts(curve, num_vectors, nullptr, n, bases_window(handle), &digits, &buckets);
+  if (digits >= kMsmMaxDigits || buckets >= kMsmMaxDigits)
+    return fail(ECC_EINVAL, "%s: the call needs 2^31 or more (point, window) digits or buckets; "
+                "use fewer vectors per call", name);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int L = field_limbs(curve, 0);
   Arg S(scalars, std::max<uint64_t>(n, 1) * num_vectors * 32), O(out, num_vectors * 2 * L * 4);
@@ -410,6 +424,13 @@ int ecc_msm_bases_ragged(void* handle, size_t num, const uint64_t* sizes, const 
   if (rows && !scalars) return fail(ECC_EINVAL, "%s: NULL pointer", name);
   if ((scalars && !aligned4(scalars)) || !aligned4(out))
     return fail(ECC_EINVAL, "%s: pointers must be 4-byte aligned", name);
+  {
+    uint64_t digits = 0, buckets = 0;
+    msm_counts(bases_curve(handle), num, sizes, 0, bases_window(handle), &digits, &buckets);
+    if (digits >= kMsmMaxDigits || buckets >= kMsmMaxDigits)
+      return fail(ECC_EINVAL, "%s: the call needs 2^31 or more (point, window) digits or buckets; "
+                  "split it", name);
+  }
   const int curve = bases_curve(handle);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int L = field_limbs(curve, 0);

@@ -77,6 +77,12 @@ cudaError_t bases_create(int curve, uint64_t n, const uint32_t* points, void** h
 cudaError_t bases_destroy(void* handle);
 cudaError_t bases_precompute(void* handle, int c, cudaStream_t st);
 int bases_window(void* handle);
+// (point, window) digits and buckets of a batch of num MSMs (sizes, or
+// size_all each when sizes is null) at the window widths the planner picks;
+// the sort and reduction index both with 32-bit words.
+void msm_counts(int curve, uint64_t num, const uint64_t* sizes, uint64_t size_all, int pre_c,
+                uint64_t* digits, uint64_t* buckets);
+constexpr uint64_t kMsmMaxDigits = 1ull << 31;
 int bases_curve(void* handle);
 uint64_t bases_count(void* handle);
 cudaError_t launch_msm_bases(void* handle, uint32_t num_vectors, const uint64_t* sizes,

@@ -117,6 +117,20 @@ cudaError_t bases_destroy(void* handle) {
 
 int bases_window(void* handle) { return static_cast<msm_detail::Bases*>(handle)->pre_c; }
 
+void msm_counts(int curve, uint64_t num, const uint64_t* sizes, uint64_t size_all, int pre_c,
+                uint64_t* digits, uint64_t* buckets) {
+  uint64_t d = 0, b = 0;
+  for (uint64_t i = 0; i < num; ++i) {
+    const uint64_t n = sizes ? sizes[i] : size_all;
+    const int c = pre_c > 0 ? pre_c : msm_window(curve, n);
+    const uint64_t W = (uint64_t)msm_detail::windows_for(curve, c);
+    d += W * n;
+    b += (pre_c > 0 ? 1 : W) << (c - 1);
+  }
+  *digits = d;
+  *buckets = b;
+}
+
 cudaError_t bases_precompute(void* handle, int c, cudaStream_t st) {
   switch (bases_curve(handle)) {
     case 2: return bases_precompute_bn254(handle, c, st);

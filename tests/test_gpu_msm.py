@@ -212,3 +212,24 @@ def test_msm_bases_precompute_rejects(gpu_lib):
         assert gpu_lib.ecc_bases_window(h) == 0
     finally:
         gpu_lib.ecc_bases_destroy(h)
+
+
+def test_msm_rejects_digit_overflow(gpu_lib):
+    """A resident-bases call whose (point, window) digits would pass 2^31 is
+    refused before any work (sizes are checked on the host)."""
+    import torch
+
+    from paper_2501_03245_gb300 import ecc
+
+    C = curves.BN254
+    n = 1 << 20
+    pts = torch.zeros((n, 16), dtype=torch.int32, device="cuda")
+    h = gpu_lib.ecc_bases_create(2, n, pts)
+    try:
+        sc = torch.zeros((8, 8), dtype=torch.int32, device="cuda")  # never read
+        out = torch.zeros((4096, 16), dtype=torch.int32, device="cuda")
+        with pytest.raises(ecc.EccError) as ex:
+            gpu_lib.ecc_msm_bases(h, 4096, sc, out)  # 4096 x 2^20 x W digits
+        assert ex.value.code == ecc.ECC_EINVAL
+    finally:
+        gpu_lib.ecc_bases_destroy(h)
