@@ -2,8 +2,10 @@
 // Table 1), used where a phase is a long dependent chain per thread with too
 // little parallelism to amortise a batch inversion: the MSM bucket reduction and
 // window combination.  Z = 0 encodes O.  Coordinates are in Montgomery form.
-// The group operations are out of line: those kernels are latency-bound, and one
-// copy per curve keeps code size and compile time small.
+// The group operations come in two forms: out of line (jac_dbl, jac_add: one
+// copy per curve keeps code size and compile time small where many call sites
+// use them) and inline (jac_dbl_inl, jac_add_inl: register-resident operands for
+// the one long chain of the window combination).
 #pragma once
 #include "ec.cuh"
 
@@ -43,7 +45,7 @@ ECC_DEV void jac_from_affine(Jac<typename C::Fp>& P, const uint32_t* x, const ui
 // 2P: S = 2((X + Y^2)^2 - X^2 - Y^4), M = 3 X^2 + a Z^4,
 // X3 = M^2 - 2S, Y3 = M (S - X3) - 8 Y^4, Z3 = (Y + Z)^2 - Y^2 - Z^2.
 template <class C>
-__device__ __noinline__ void jac_dbl(Jac<typename C::Fp>& R, const Jac<typename C::Fp>& P) {
+ECC_DEV void jac_dbl_inl(Jac<typename C::Fp>& R, const Jac<typename C::Fp>& P) {
   using F = typename C::Fp;
   constexpr int N = F::N;
   if (jac_is_inf<C>(P) || fe_is_zero<F>(P.Y)) {
@@ -90,6 +92,12 @@ __device__ __noinline__ void jac_dbl(Jac<typename C::Fp>& R, const Jac<typename 
 
 // Shared tail of the additions: given U1, S1, H = U2 - U1, r = S2 - S1 and
 // Z3 / H, X3 = r^2 - H^3 - 2 U1 H^2, Y3 = r (U1 H^2 - X3) - S1 H^3.
+// Out of line: one copy per curve for the kernels that call it from many places.
+template <class C>
+__device__ __noinline__ void jac_dbl(Jac<typename C::Fp>& R, const Jac<typename C::Fp>& P) {
+  jac_dbl_inl<C>(R, P);
+}
+
 template <class C>
 ECC_DEV void jac_add_tail(Jac<typename C::Fp>& R, const uint32_t* U1, const uint32_t* S1,
                           const uint32_t* H, const uint32_t* r, const uint32_t* Z3) {
@@ -114,7 +122,7 @@ ECC_DEV void jac_add_tail(Jac<typename C::Fp>& R, const uint32_t* U1, const uint
 
 // R = P + Q, both Jacobian (every case of the group law).
 template <class C>
-__device__ __noinline__ void jac_add(Jac<typename C::Fp>& R, const Jac<typename C::Fp>& P,
+ECC_DEV void jac_add_inl(Jac<typename C::Fp>& R, const Jac<typename C::Fp>& P,
                      const Jac<typename C::Fp>& Q) {
   using F = typename C::Fp;
   constexpr int N = F::N;
@@ -148,6 +156,12 @@ __device__ __noinline__ void jac_add(Jac<typename C::Fp>& R, const Jac<typename 
   mont_mul<F>(Z3, P.Z, Q.Z);
   mont_mul<F>(Z3, Z3, H);
   jac_add_tail<C>(R, U1, S1, H, r, Z3);
+}
+
+template <class C>
+__device__ __noinline__ void jac_add(Jac<typename C::Fp>& R, const Jac<typename C::Fp>& P,
+                                     const Jac<typename C::Fp>& Q) {
+  jac_add_inl<C>(R, P, Q);
 }
 
 // R = P + (x, y) with the second operand affine ((0, 0) = O).

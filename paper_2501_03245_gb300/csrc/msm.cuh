@@ -732,8 +732,8 @@ __global__ void k_msm_combine(const MsmInst* inst, const uint64_t* fin, uint32_t
   const Jac<F>* Sw = S + fin[id];
   Jac<F> acc = Sw[W - 1];
   for (int w = (int)W - 2; w >= 0; --w) {
-    for (uint32_t s = 0; s < c; ++s) jac_dbl<C>(acc, acc);
-    jac_add<C>(acc, acc, Sw[w]);
+    for (uint32_t s = 0; s < c; ++s) jac_dbl_inl<C>(acc, acc);
+    jac_add_inl<C>(acc, acc, Sw[w]);
   }
   uint32_t x[N], y[N];
   jac_to_affine<C>(x, y, acc);
