@@ -19,11 +19,11 @@ TRICK_MODMUL_PER_ELEMENT = 3
 BATCH_PADD_MODMUL = PADD_FORMULA_MODMUL + TRICK_MODMUL_PER_ELEMENT   # 6
 BATCH_PDBL_MODMUL = PDBL_FORMULA_MODMUL + TRICK_MODMUL_PER_ELEMENT   # 7
 
-# ECDSA verification schedule of the verification kernel
-Q_WINDOWS = 65          # signed radix-16 digits of u2 (64 + carry digit)
-Q_DOUBLINGS = 64 * 4    # 4 doublings between consecutive windows
+# ECDSA verification schedule of the verification kernel: signed windows of
+# Q_WINDOW_BITS bits for u2 (the kernel's kQW), a table {Q .. 2^(w-1) Q} whose
+# powers of two are doublings and the rest additions, 8-bit fixed-base comb.
+Q_WINDOW_BITS = 5
 G_COMB_ADDS = 32        # fixed-base comb, 8-bit windows
-TABLE_DBL, TABLE_ADD = 4, 3   # {2Q, 4Q, 6Q, 8Q} doublings, {3Q, 5Q, 7Q} additions
 FINAL_ADDS = 1          # R = u1 G + u2 Q
 SCALAR_MODMUL = 3 + 2 + 2   # batched s^-1 (trick), u1 and u2, two conversions out
 PREP_MODMUL = 5 + 4         # five conversions into Montgomery form, on-curve check
@@ -34,10 +34,25 @@ def imad_per_modmul(limbs):
     return 2 * limbs * limbs + limbs
 
 
-def verify_modmul():
+def q_digits(w=Q_WINDOW_BITS):
+    """Signed radix-2^w digits of a 256-bit scalar: ceil(256 / w), plus a carry
+    digit when the top digit holds at least w - 1 bits."""
+    top_bits = 256 - w * ((256 - 1) // w)
+    return -(-256 // w) + (1 if top_bits >= w - 1 else 0)
+
+
+def verify_schedule(w=Q_WINDOW_BITS):
+    """(batched PDBL, batched PADD) per verification."""
+    digits = q_digits(w)
+    table = 1 << (w - 1)
+    dbl = (digits - 1) * w + (w - 1)            # ladder + table powers of two
+    add = digits + G_COMB_ADDS + (table - 1 - (w - 1)) + FINAL_ADDS
+    return dbl, add
+
+
+def verify_modmul(w=Q_WINDOW_BITS):
     """Algorithmic modmul per ECDSA verification (256-bit curves)."""
-    dbl = Q_DOUBLINGS + TABLE_DBL
-    add = Q_WINDOWS + G_COMB_ADDS + TABLE_ADD + FINAL_ADDS
+    dbl, add = verify_schedule(w)
     return dbl * BATCH_PDBL_MODMUL + add * BATCH_PADD_MODMUL + SCALAR_MODMUL + PREP_MODMUL
 
 

@@ -17,9 +17,9 @@ cudaError_t verify(size_t n, const uint8_t* hash, const uint8_t* r, const uint8_
   const uint4* tg = nullptr;
   cudaError_t e = gtable(curve, &tg, st);
   if (e != cudaSuccess) return e;
-  // workspace: S, E, Rn (Fn) | TQ x,y (8n each) | AQ, AG | M | D2 | U1B | status
+  // workspace: S, E, Rn (Fn) | TQ x,y (kQTable n each) | AQ, AG | M | D2 | U1B | status
   const size_t fe = soa_bytes<Fp>(n);
-  const size_t bytes = 3 * fe + 16 * fe + 4 * fe + fe + 65 * n + 32 * n + n + 256;
+  const size_t bytes = 3 * fe + 2 * kQTable * fe + 4 * fe + fe + (kQDigits + 32 + 1) * n + 256;
   Scratch ws;
   e = ws.alloc(bytes, st);
   if (e != cudaSuccess) return e;
@@ -35,14 +35,15 @@ cudaError_t verify(size_t n, const uint8_t* hash, const uint8_t* r, const uint8_
   a.S = SoA<Fn>{v + 0 * q, n};
   a.E = SoA<Fn>{v + 1 * q, n};
   a.Rn = SoA<Fn>{v + 2 * q, n};
-  a.TQ = PtSoA<Fp>{SoA<Fp>{v + 3 * q, 8 * n}, SoA<Fp>{v + 11 * q, 8 * n}};
-  a.AQ = PtSoA<Fp>{SoA<Fp>{v + 19 * q, n}, SoA<Fp>{v + 20 * q, n}};
-  a.AG = PtSoA<Fp>{SoA<Fp>{v + 21 * q, n}, SoA<Fp>{v + 22 * q, n}};
-  a.M = SoA<Fp>{v + 23 * q, n};
-  uint8_t* tail = reinterpret_cast<uint8_t*>(v + 24 * q);
+  const size_t T = kQTable;
+  a.TQ = PtSoA<Fp>{SoA<Fp>{v + 3 * q, T * n}, SoA<Fp>{v + (3 + T) * q, T * n}};
+  a.AQ = PtSoA<Fp>{SoA<Fp>{v + (3 + 2 * T) * q, n}, SoA<Fp>{v + (4 + 2 * T) * q, n}};
+  a.AG = PtSoA<Fp>{SoA<Fp>{v + (5 + 2 * T) * q, n}, SoA<Fp>{v + (6 + 2 * T) * q, n}};
+  a.M = SoA<Fp>{v + (7 + 2 * T) * q, n};
+  uint8_t* tail = reinterpret_cast<uint8_t*>(v + (8 + 2 * T) * q);
   a.D2 = reinterpret_cast<int8_t*>(tail);
-  a.U1B = tail + 65 * n;
-  a.status = tail + 97 * n;
+  a.U1B = tail + kQDigits * n;
+  a.status = tail + (kQDigits + 32) * n;
   const size_t te = 32 * 256;
   a.TG = PtSoA<Fp>{SoA<Fp>{const_cast<uint4*>(tg), te}, SoA<Fp>{const_cast<uint4*>(tg) + soa_bytes<Fp>(te) / 16, te}};
   size_t ctas = (size_t)device_sm_count() * kGasCtasPerSm;

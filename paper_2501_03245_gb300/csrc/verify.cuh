@@ -8,12 +8,15 @@
 //
 //   * u1 G: fixed-base comb over a precomputed table TG[j][v] = v 2^(8j) G
 //     (8-bit windows, 32 table additions, no doublings; Section 2.1.1 on FPMUL);
-//   * u2 Q: signed 4-bit fixed windows, most significant first, with a per-item
-//     table {Q, 2Q, ..., 8Q} built in three batched rounds; 64 x 4 doublings and
-//     65 additions.  Every lane follows the same schedule (digit 0 is a no-op
-//     addition of O), so warps never diverge on the scalar.
-//   * one G-table addition rides in every second addition round, so its
-//     denominator shares that round's chain (the fusion idea of Section 3.4).
+//   * u2 Q: signed kQW-bit fixed windows, most significant first, with a
+//     per-item table {Q, 2Q, ..., 2^(kQW-1) Q} built in batched rounds of at most
+//     four additions; (kQDigits - 1) x kQW doublings and kQDigits additions.
+//     Every lane follows the same schedule (digit 0 is a no-op addition of O),
+//     so warps never diverge on the scalar.  A wider window trades table
+//     rounds and memory for fewer main-loop rounds, each of which costs one
+//     CTA-wide inversion.
+//   * the 32 G-table additions ride in the last 32 addition rounds, so their
+//     denominators share those rounds' chains (the fusion idea of Section 3.4).
 //
 // Each CTA owns a contiguous slice of the batch for the whole verification:
 // every round is compress -> per-CTA inversion -> DCWPA over the same slice, so
@@ -34,17 +37,24 @@ struct VerifyArgs {
   const uint32_t* pub;   // n x 64 bytes (x || y) big-endian
   uint8_t* ok;
   SoA<Fn> S, E, Rn;      // s, e mod n, r in Montgomery form (mod n)
-  PtSoA<Fp> TQ;          // per-item table, element (k - 1) * n + i holds k Q_i
+  PtSoA<Fp> TQ;          // per-item table, element (k - 1) * n + i holds k Q_i, k <= kQTable
   PtSoA<Fp> AQ, AG;      // accumulators of u2 Q and u1 G
   SoA<Fp> M;             // running products of the compress step
-  int8_t* D2;            // signed 4-bit digits of u2: D2[w * n + i], w = 0..64
+  int8_t* D2;            // signed kQW-bit digits of u2: D2[w * n + i], w < kQDigits
   uint8_t* U1B;          // bytes of u1: U1B[j * n + i], j = 0..31
   uint8_t* status;       // 1 = well-formed input
   PtSoA<Fp> TG;          // fixed-base table, entry j * 256 + v
   size_t per_cta;
 };
 
-constexpr int kQDigits = 65;  // signed radix-16 digits of a 256-bit scalar
+// Signed radix-2^kQW digits of a 256-bit scalar: ceil(256 / kQW) digits, plus
+// one when the top digit's bits (256 mod kQW, or kQW) can reach 2^(kQW-1) - 1
+// and so carry out.
+constexpr int kQW = 5;
+constexpr int kQTable = 1 << (kQW - 1);
+constexpr int kQTopBits = 256 - kQW * ((256 - 1) / kQW);
+constexpr int kQDigits = (256 + kQW - 1) / kQW + ((1 << kQTopBits) - 1 + 1 >= (1 << (kQW - 1)) ? 1 : 0);
+static_assert(kQDigits >= 32, "the G additions ride in 32 addition rounds");
 
 ECC_DEV uint32_t bswap32(uint32_t x) { return __byte_perm(x, 0, 0x0123); }
 
@@ -170,33 +180,35 @@ struct ScalarRound {
     from_mont<Fn>(u, u);
     int carry = 0;
 #pragma unroll
-    for (int w = 0; w < 64; ++w) {
-      int v = (int)((u[w >> 3] >> (4 * (w & 7))) & 15u) + carry;
-      carry = v >= 8 ? 1 : 0;
-      a->D2[w * n + i] = (int8_t)(v - 16 * carry);
+    for (int w = 0; w < kQDigits; ++w) {
+      // bits [kQW w, kQW w + kQW) of u (zero above bit 255)
+      const int pos = kQW * w, word = pos >> 5, sh = pos & 31;
+      uint64_t bits = word < 8 ? u[word] : 0u;
+      if (word + 1 < 8) bits |= (uint64_t)u[word + 1] << 32;
+      const int v = (int)((bits >> sh) & (uint64_t)(kQTable * 2 - 1)) + carry;
+      carry = v >= kQTable ? 1 : 0;
+      a->D2[w * n + i] = (int8_t)(v - 2 * kQTable * carry);
     }
-    a->D2[64 * n + i] = (int8_t)carry;
   }
 };
 
-// Per-item table {Q, ..., 8Q}: round 1: 2Q; round 2: 3Q, 4Q; round 3: 5Q..8Q.
-template <class C, int K>
+// Per-item table {Q, ..., kQTable Q}: a round makes OPS consecutive multiples
+// k = K0 .. K0 + OPS - 1 as B Q + (k - B) Q with B the largest power of two
+// below K0 (2Q = Q + Q by the doubling branch of the addition): 2Q; 3Q, 4Q;
+// 5Q..8Q; 9Q..12Q, 13Q..16Q; ...
+template <class C, int K0, int OPS_>
 struct TableRound {
   using F = typename C::Fp;
   static constexpr int N = F::N;
-  static constexpr int OPS = K == 1 ? 1 : (K == 2 ? 2 : 4);
+  static constexpr int OPS = OPS_;
+  static constexpr int B = K0 <= 2 ? 1 : (K0 <= 4 ? 2 : (K0 <= 8 ? 4 : (K0 <= 16 ? 8 : 16)));
   const VerifyArgs<C>* a;
   int kind[OPS];
   ECC_DEV static void op(int j, int& dst, int& s1, int& s2) {
     // multiples k of Q are stored at table index k - 1
-    if (K == 1) {
-      dst = 2; s1 = 1; s2 = 1;
-    } else if (K == 2) {
-      dst = 3 + j; s1 = 2; s2 = j == 0 ? 1 : 2;
-    } else {
-      const int d[4] = {5, 6, 7, 8}, x[4] = {4, 3, 4, 4}, y[4] = {1, 3, 3, 4};
-      dst = d[j]; s1 = x[j]; s2 = y[j];
-    }
+    dst = K0 + j;
+    s1 = B;
+    s2 = K0 + j - B;
   }
   ECC_DEV void operands(size_t i, int j, uint32_t* xp, uint32_t* yp, uint32_t* xt, uint32_t* yt) {
     int dst, s1, s2;
@@ -351,22 +363,38 @@ __global__ void __launch_bounds__(BLOCK, kGasResidentThreads / BLOCK) k_verify(V
     batch_round<Fn, BLOCK>(rd, begin, end, SoA<Fn>{a.M.vec, a.M.stride}, sm);
   }
   {
-    TableRound<C, 1> r1{&a};
+    TableRound<C, 2, 1> r1{&a};
     batch_round<Fp, BLOCK>(r1, begin, end, a.M, sm);
-    TableRound<C, 2> r2{&a};
+    TableRound<C, 3, 2> r2{&a};
     batch_round<Fp, BLOCK>(r2, begin, end, a.M, sm);
-    TableRound<C, 3> r3{&a};
+    TableRound<C, 5, 4> r3{&a};
     batch_round<Fp, BLOCK>(r3, begin, end, a.M, sm);
+    if (kQTable >= 16) {
+      TableRound<C, 9, 4> r4{&a};
+      batch_round<Fp, BLOCK>(r4, begin, end, a.M, sm);
+      TableRound<C, 13, 4> r5{&a};
+      batch_round<Fp, BLOCK>(r5, begin, end, a.M, sm);
+    }
+    if (kQTable >= 32) {
+      TableRound<C, 17, 4> r6{&a};
+      batch_round<Fp, BLOCK>(r6, begin, end, a.M, sm);
+      TableRound<C, 21, 4> r7{&a};
+      batch_round<Fp, BLOCK>(r7, begin, end, a.M, sm);
+      TableRound<C, 25, 4> r8{&a};
+      batch_round<Fp, BLOCK>(r8, begin, end, a.M, sm);
+      TableRound<C, 29, 4> r9{&a};
+      batch_round<Fp, BLOCK>(r9, begin, end, a.M, sm);
+    }
   }
   for (int w = kQDigits - 1; w >= 0; --w) {
     if (w < kQDigits - 1) {
-      for (int k = 0; k < 4; ++k) {
+      for (int k = 0; k < kQW; ++k) {
         DblRound<C> rd{&a};
         batch_round<Fp, BLOCK>(rd, begin, end, a.M, sm);
       }
     }
-    if ((w & 1) == 0 && w < 64) {
-      AddRound<C, true> rd{&a, w, w >> 1};
+    if (w < 32) {  // G-table window jg = w rides along
+      AddRound<C, true> rd{&a, w, w};
       batch_round<Fp, BLOCK>(rd, begin, end, a.M, sm);
     } else {
       AddRound<C, false> rd{&a, w, 0};

@@ -29,10 +29,27 @@ def test_break_even():
 
 
 def test_verify_count_structure():
+    # w = 5: 52 digits (51 x 5 ladder doublings), table {Q..16Q}: 4 doublings,
+    # 11 additions; 52 + 32 + 11 + 1 additions in all
+    assert [costmodel.q_digits(w) for w in (4, 5, 6)] == [65, 52, 43]
+    assert costmodel.verify_schedule(5) == (259, 96)
+    assert costmodel.verify_schedule(4) == (259, 102)
     m = costmodel.verify_modmul()
-    assert m == 260 * 7 + 101 * 6 + 7 + 9
+    assert m == 259 * 7 + 96 * 6 + 7 + 9
     assert costmodel.verify_imad() == m * 136
     assert costmodel.fpmul_modmul() == 32 * 6
+
+
+def test_verify_schedule_matches_the_kernel():
+    """The cost model's window width is the verification kernel's (read from
+    the CUDA source, whose digit count the same rule gives)."""
+    import os
+    import re
+
+    src = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                       "paper_2501_03245_gb300", "csrc", "verify.cuh")
+    text = open(src).read()
+    assert int(re.search(r"constexpr int kQW = (\d+);", text).group(1)) == costmodel.Q_WINDOW_BITS
 
 
 def test_msm_precomputed_count():
