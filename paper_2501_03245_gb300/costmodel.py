@@ -74,6 +74,12 @@ def break_even_batch(inv_over_mul=100):
     return n
 
 
+def msm_windows(scalar_bits, c):
+    """Signed c-bit windows (c >= 2) of a scalar below 2^scalar_bits: the digits
+    reach one bit past the scalar, since a top digit above 2^(c-1) carries out."""
+    return -(-(scalar_bits + 1) // c)
+
+
 def msm_modmul(n_points, windows, c, buckets_touched=None):
     """Algorithmic modmul of one Pippenger MSM with batch-affine bucket
     accumulation: one batched PADD per (point, window) digit, the bucket

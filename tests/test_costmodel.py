@@ -59,3 +59,27 @@ def test_msm_precomputed_count():
     assert costmodel.msm_modmul_precomputed(n, W, c) == 6 * n * W + 2 * 6 * (1 << (c - 1))
     assert costmodel.msm_modmul(n, W, c) - costmodel.msm_modmul_precomputed(n, W, c) == \
         2 * 6 * (W - 1) * (1 << (c - 1)) + W * (7 * c + 6)
+
+
+def _signed_digits(k, c):
+    """Signed radix-2^c recoding with digits in [-2^(c-1)+1, 2^(c-1)]."""
+    out = []
+    while k:
+        d = k & ((1 << c) - 1)
+        if d > (1 << (c - 1)):
+            d -= 1 << c
+        out.append(d)
+        k = (k - d) >> c
+    return out
+
+
+def test_msm_windows_by_brute_force():
+    # every scalar below 2^b recodes into msm_windows(b, c) signed digits, and
+    # some scalar needs all of them (c >= 2, the library's range: at c = 1 the
+    # digit set is {0, 1} and never carries)
+    for b in range(1, 11):
+        for c in range(2, 8):
+            need = max(len(_signed_digits(k, c)) for k in range(1 << b))
+            assert need == costmodel.msm_windows(b, c), (b, c)
+    assert costmodel.msm_windows(255, 16) == 16   # BLS12-381 r
+    assert costmodel.msm_windows(254, 13) == 20   # BN254 r
