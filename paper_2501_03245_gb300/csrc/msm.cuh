@@ -172,21 +172,40 @@ struct AccArgs {
 };
 
 template <class C>
-ECC_DEV void load_base(const AccArgs<C>& a, uint32_t v, uint32_t* x, uint32_t* y) {
-  using F = typename C::Fp;
-  constexpr int N = F::N;
-  const uint4* p = reinterpret_cast<const uint4*>(a.bases + (uint64_t)(v & 0x7fffffffu) * 2 * N);
+ECC_DEV const uint4* base_ptr(const AccArgs<C>& a, uint32_t v) {
+  return reinterpret_cast<const uint4*>(a.bases + (uint64_t)(v & 0x7fffffffu) * 2 * C::Fp::N);
+}
+
+// x of the base a digit names (the sign only touches y)
+template <class C>
+ECC_DEV void load_base_x(const AccArgs<C>& a, uint32_t v, uint32_t* x) {
+  constexpr int N = C::Fp::N;
+  const uint4* p = base_ptr(a, v);
 #pragma unroll
   for (int g = 0; g < N / 4; ++g) {
     const uint4 t = p[g];
     x[4 * g] = t.x; x[4 * g + 1] = t.y; x[4 * g + 2] = t.z; x[4 * g + 3] = t.w;
   }
+}
+
+// y of the base a digit names, negated for a negative digit
+template <class C>
+ECC_DEV void load_base_y(const AccArgs<C>& a, uint32_t v, uint32_t* y) {
+  using F = typename C::Fp;
+  constexpr int N = F::N;
+  const uint4* p = base_ptr(a, v);
 #pragma unroll
   for (int g = 0; g < N / 4; ++g) {
     const uint4 t = p[N / 4 + g];
     y[4 * g] = t.x; y[4 * g + 1] = t.y; y[4 * g + 2] = t.z; y[4 * g + 3] = t.w;
   }
   if (v & 0x80000000u) fe_neg<F>(y, y);
+}
+
+template <class C>
+ECC_DEV void load_base(const AccArgs<C>& a, uint32_t v, uint32_t* x, uint32_t* y) {
+  load_base_x<C>(a, v, x);
+  load_base_y<C>(a, v, y);
 }
 
 template <class C>
@@ -205,18 +224,52 @@ ECC_DEV uint32_t bucket_of(const uint32_t* off, uint32_t lo, uint32_t n, uint32_
   return lo;
 }
 
-template <class C>
+// One round of the chunked running sums: entry j of every chunk is added to
+// the chunk's running sum S (or starts a new one at a bucket boundary).
+// Compress (den_c) loads only x of S and of the base, as the compress step of
+// Section 3.3 does; y is needed only when an operand may be O (x = 0) or the
+// x coordinates agree (doubling or P = -T), which random inputs almost never
+// hit.  For 8-limb fields the DCWPA step (den_d) loads both operands once and
+// keeps them in registers for finish, so no denominator array is written; the
+// 12-limb fields have no registers to spare and store the denominator in
+// compress instead.
+// A thread's items are BLOCK chunks apart.  Each pass issues the first-level
+// loads of the thread's next item (its sorted entry, its chunk's current
+// bucket and, for 8-limb fields in compress, x of its running sum) before the
+// current item's arithmetic, so the dependent loads behind them (the base
+// gather, the bucket offsets) start as soon as the next item begins.
+template <class C, int BLOCK>
 struct AccRound {
   using F = typename C::Fp;
   static constexpr int N = F::N;
   static constexpr int OPS = 1;
+  static constexpr bool kHold = N <= 8;
   const AccArgs<C>* a;
   int j;
   uint32_t entries;
-  uint32_t bucket, prev;
+  uint64_t begin, end;  // this CTA's chunks
+  uint64_t nc = ~0ull;  // chunk whose loads below were issued ahead
+  uint32_t nv, ncur;
+  uint32_t nxs[kHold ? N : 1];
+  uint32_t bucket, prev, cv;
   bool start, live;
-  // Entry j of chunk c: its bucket, and whether it starts a new running sum.
-  ECC_DEV void classify(size_t c) {
+  int kind;
+  uint32_t xs[kHold ? N : 1], ys[kHold ? N : 1], xp[kHold ? N : 1], yp[kHold ? N : 1];
+  // first-level loads of chunk c: entry j and (j > 0) the chunk's current bucket
+  ECC_DEV void fetch(uint64_t c, uint32_t& v, uint32_t& pb) const {
+    v = a->vals[(uint64_t)j * a->n_chunks + c];
+    pb = j > 0 ? a->cur[c] : 0u;
+  }
+  ECC_DEV void ahead(uint64_t c, bool with_x) {
+    nc = c;
+    fetch(c, nv, ncur);
+    if constexpr (kHold) {
+      if (with_x) a->S.x.load(c, nxs);
+    }
+  }
+  // Entry j of chunk c: its bucket, and whether it starts a new running sum
+  // (pb = the chunk's bucket before this entry).
+  ECC_DEV void classify(uint64_t c, uint32_t pb) {
     const uint32_t p = (uint32_t)(c * kAccChunk + j);
     live = p < entries;
     if (!live) return;
@@ -225,7 +278,7 @@ struct AccRound {
       start = true;
       return;
     }
-    prev = a->cur[c];
+    prev = pb;
     if (p < a->off[prev + 1]) {
       bucket = prev;
       start = false;
@@ -236,36 +289,93 @@ struct AccRound {
     if (a->off[bucket + 1] <= p) bucket = bucket_of(a->off, bucket + 1, a->n_buckets, p);
   }
   ECC_DEV void den_c(size_t c, int, uint32_t* d) {
-    classify(c);
+    uint32_t v, pb, x1[N];
+    if (nc == c) {
+      v = nv;
+      pb = ncur;
+      if constexpr (kHold) fe_copy<F>(x1, nxs);
+    } else {
+      fetch(c, v, pb);
+      if constexpr (kHold) a->S.x.load(c, x1);
+    }
+    if (c + BLOCK < end) ahead(c + BLOCK, true);
+    classify(c, pb);
     if (!live || start) {
       fe_set_one<F>(d);
     } else {
-      uint32_t xs[N], ys[N], xp[N], yp[N];
-      a->S.load(c, xs, ys);
-      load_base<C>(*a, a->vals[(uint64_t)j * a->n_chunks + c], xp, yp);
-      add_den<C>(d, xs, ys, xp, yp);
-    }
-    a->D.store(c, d);
-  }
-  ECC_DEV void den_d(size_t c, int, uint32_t* d) { a->D.load(c, d); }
-  ECC_DEV void finish(size_t c, const uint32_t (*inv)[N]) {
-    classify(c);
-    if (!live) return;
-    uint32_t xs[N], ys[N], xp[N], yp[N];
-    load_base<C>(*a, a->vals[(uint64_t)j * a->n_chunks + c], xp, yp);
-    if (start) {
-      if (j > 0) {
-        a->S.load(c, xs, ys);
-        a->partial.store(partial_slot(*a, prev, c), xs, ys);
+      uint32_t x2[N];
+      if constexpr (!kHold) a->S.x.load(c, x1);
+      load_base_x<C>(*a, v, x2);
+      if (fe_is_zero<F>(x1) || fe_is_zero<F>(x2) || fe_eq<F>(x1, x2)) {
+        uint32_t y1[N], y2[N];
+        a->S.y.load(c, y1);
+        load_base_y<C>(*a, v, y2);
+        add_den<C>(d, x1, y1, x2, y2);
+      } else {
+        fe_sub<F>(d, x2, x1);
       }
-      a->S.store(c, xp, yp);
-    } else {
-      a->S.load(c, xs, ys);
-      const int kind = add_kind<C>(xs, ys, xp, yp);
-      add_finish<C>(xs, ys, kind, inv[0], xs, ys, xp, yp);
-      a->S.store(c, xs, ys);
     }
-    if (start) a->cur[c] = bucket;
+    if (!kHold) a->D.store(c, d);
+  }
+  ECC_DEV void den_d(size_t c, int, uint32_t* d) {
+    if constexpr (kHold) {
+      // DCWPA walks the items downwards
+      uint32_t pb;
+      if (nc == c) {
+        cv = nv;
+        pb = ncur;
+      } else {
+        fetch(c, cv, pb);
+      }
+      if (c >= begin + BLOCK) ahead(c - BLOCK, false);
+      classify(c, pb);
+      if (!live || start) {
+        fe_set_one<F>(d);
+      } else {
+        a->S.load(c, xs, ys);
+        load_base<C>(*a, cv, xp, yp);
+        kind = add_den<C>(d, xs, ys, xp, yp);
+      }
+    } else {
+      a->D.load(c, d);
+    }
+  }
+  ECC_DEV void finish(size_t c, const uint32_t (*inv)[N]) {
+    if constexpr (kHold) {
+      if (!live) return;
+      if (start) {
+        load_base<C>(*a, cv, xp, yp);
+        if (j > 0) {
+          a->S.load(c, xs, ys);
+          a->partial.store(partial_slot(*a, prev, c), xs, ys);
+        }
+        a->S.store(c, xp, yp);
+        a->cur[c] = bucket;
+      } else {
+        add_finish<C>(xs, ys, kind, inv[0], xs, ys, xp, yp);
+        a->S.store(c, xs, ys);
+      }
+    } else {
+      uint32_t v, pb;
+      fetch(c, v, pb);
+      classify(c, pb);
+      if (!live) return;
+      uint32_t x1[N], y1[N], x2[N], y2[N];
+      load_base<C>(*a, v, x2, y2);
+      if (start) {
+        if (j > 0) {
+          a->S.load(c, x1, y1);
+          a->partial.store(partial_slot(*a, prev, c), x1, y1);
+        }
+        a->S.store(c, x2, y2);
+        a->cur[c] = bucket;
+      } else {
+        a->S.load(c, x1, y1);
+        const int k = add_kind<C>(x1, y1, x2, y2);
+        add_finish<C>(x1, y1, k, inv[0], x1, y1, x2, y2);
+        a->S.store(c, x1, y1);
+      }
+    }
   }
 };
 
@@ -281,7 +391,7 @@ __global__ void __launch_bounds__(BLOCK, kGasResidentThreads / BLOCK) k_msm_accu
   if (end > used) end = used;
   if (end < begin) end = begin;
   for (int j = 0; j < kAccChunk; ++j) {
-    AccRound<C> rd{&a, j, entries};
+    AccRound<C, BLOCK> rd{&a, j, entries, begin, end};
     batch_round<F, BLOCK>(rd, begin, end, a.M, sm);
   }
   // flush the last running sum of every chunk

@@ -51,7 +51,11 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
   const uint64_t sz_kv = up(kAccChunk * NC * 4), sz_cur = up(NC * 4);
   const uint64_t sz_S = soa_bytes<F>(NC), sz_P = soa_bytes<F>(n_part);
   const uint64_t sz_ops = up(n_part * 4);
-  const uint64_t bytes = sz_inst + 5 * sz_b1 + sz_kv + sz_cur + 4 * sz_S + 3 * sz_P + sz_ops + 256;
+  // per chunk: running sum (x, y), prefix product and, where the accumulation
+  // does not keep its operands in registers, the round's denominator
+  constexpr bool kHold = AccRound<C, kAccBlock>::kHold;
+  constexpr uint64_t kChunkArrays = kHold ? 3 : 4;
+  const uint64_t bytes = sz_inst + 5 * sz_b1 + sz_kv + sz_cur + kChunkArrays * sz_S + 3 * sz_P + sz_ops + 256;
   Scratch ws;
   cudaError_t e = ws.alloc(bytes, st);
   if (e != cudaSuccess) return e;
@@ -65,7 +69,7 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
   uint32_t* poff = reinterpret_cast<uint32_t*>(take(sz_b1));
   uint32_t* vals = reinterpret_cast<uint32_t*>(take(sz_kv));
   uint32_t* cur = reinterpret_cast<uint32_t*>(take(sz_cur));
-  uint4* sbuf = reinterpret_cast<uint4*>(take(4 * sz_S));
+  uint4* sbuf = reinterpret_cast<uint4*>(take(kChunkArrays * sz_S));
   uint4* pbuf = reinterpret_cast<uint4*>(take(3 * sz_P));
   uint32_t* fold_ops = reinterpret_cast<uint32_t*>(take(sz_ops));
   e = upload_words(d_inst, L.inst.data(), num * sizeof(MsmInst), st);
@@ -95,7 +99,7 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
   a.bases = bases_mont;
   a.S = PtSoA<F>{SoA<F>{sbuf, NC}, SoA<F>{sbuf + sz_S / 16, NC}};
   a.M = SoA<F>{sbuf + 2 * sz_S / 16, NC};
-  a.D = SoA<F>{sbuf + 3 * sz_S / 16, NC};
+  a.D = kHold ? SoA<F>{nullptr, NC} : SoA<F>{sbuf + 3 * sz_S / 16, NC};
   a.partial = PtSoA<F>{SoA<F>{pbuf, n_part}, SoA<F>{pbuf + sz_P / 16, n_part}};
   uint64_t ctas = (uint64_t)device_sm_count() * kGasCtasPerSm;
   uint64_t per = (NC + ctas - 1) / ctas;
