@@ -374,6 +374,14 @@ def bench_ragged(ecc, costmodel, synth, torch, peak, rank, world=1):
                                   "+ c PDBL and 1 PADD per window, 136 wide mul-adds per modmul"}}
 
 
+def verify_config(n):
+    """The verification workload's config, shared by both arms."""
+    shape = "2^20" if n == N_VERIFY else str(n)
+    return {"workload": f"ECDSA verify, NIST P-256, {shape} seeded triples per GPU, 1/16 corrupted",
+            "curve": "P-256", "batch": n, "l2": "working set > L2 (inputs 160 MiB + "
+            "per-item state ~0.8 GiB per step)"}
+
+
 def run_reference(args):
     """--impl reference: the oracle as it stands on the host cores, on the same
     workload (bounded samples per step); rank 0 only."""
@@ -402,11 +410,11 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": "ECDSA verify, NIST P-256, 2^20 seeded triples, 1/16 corrupted "
-                               f"(reference: {sample}-triple bounded sample per step)",
-                   "curve": "P-256", "batch": N_VERIFY},
+        "config": verify_config(N_VERIFY),
         "cpu_baseline": {"value": value, "unit": "verifies/s", "cores": threads, "kind": "oracle",
-                         "sample": f"{sample} triples per step, plain C++ bigint oracle"},
+                         "sample": f"{sample} triples per step by the workload's recipe (seed "
+                                   f"{synth.SEED_BASE + 1:#x}, 1/16 corrupted), plain C++ bigint "
+                                   f"oracle (Barrett + Jacobian), {threads} threads"},
         "e2e": {"value": value, "unit": "verifies/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -512,9 +520,7 @@ def run_ours(args):
         "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": total_s / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic",
-        "config": {"workload": "ECDSA verify, NIST P-256, 2^20 seeded triples per GPU, 1/16 corrupted",
-                   "curve": "P-256", "batch": n, "l2": "working set > L2 (inputs 160 MiB + "
-                   "per-item state ~0.8 GiB per step)", "valid_signatures": n_valid},
+        "config": verify_config(n), "valid_signatures": n_valid,
         "roofline": {"bound": "alu", "kernel": "k_verify<P256>", "achieved": achieved / 1e12,
                      "peak": peak / 1e12, "unit": "T IMAD.WIDE/s", "frac": achieved / peak,
                      "traffic": verify_traffic(n), "traffic_unit": "DRAM bytes per launch",
