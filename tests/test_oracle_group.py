@@ -107,3 +107,19 @@ def test_msm_definition_and_closed_form():
     assert ec.add(C, ec.msm(C, k, P), ec.msm(C, k2, P)) == ec.msm(C, [x + y for x, y in zip(k, k2)], P)
     assert ec.msm(C, [0] * 10, P) is None
     assert ec.msm(C, [], []) is None
+
+
+@pytest.mark.parametrize("C", list(curves.BY_ID.values()), ids=lambda c: c.name)
+def test_large_curve_associativity_random_triples(C):
+    # 2500 triples per curve (12,500 over the five curves) from a pool of random
+    # multiples of G, its negatives, O and repeated points, so the exceptional
+    # branches (P = T doubles, P = -T cancels, O passes through) meet the
+    # regular ones in every position of (P + T) + U = P + (T + U)
+    rng = random.Random(C.n & 0xFFFFFF)
+    base = [ec.mul(C, rng.randrange(1, C.n), C.G) for _ in range(24)]
+    pool = base + [ec.neg(C, P) for P in base[:6]] + [None]
+    for _ in range(2500):
+        P, T, U = rng.choice(pool), rng.choice(pool), rng.choice(pool)
+        if rng.random() < 0.1:
+            T = P
+        assert ec.add(C, ec.add(C, P, T), U) == ec.add(C, P, ec.add(C, T, U))
