@@ -170,9 +170,9 @@ def gen_inputs(ecc, synth, torch, n, seed, curve=CURVE_P256):
 # dram__bytes_write.sum, one ncu capture; summary and command in
 # profiles/k_verify_p256_2e20_dram.md), valid only for the kernel sources it was
 # taken on: reported as null once any of them has changed.
-VERIFY_TRAFFIC = {"bytes": 82872315136 + 34264189184, "batch": 1 << 20, "digest": "fe31e1eb96685a8d",
-                  "sources": ["verify.cuh", "ec.cuh", "fp.cuh", "inv.cuh", "ptx.cuh", "curves_gen.cuh",
-                              "k_verify.cu"]}
+VERIFY_TRAFFIC = {"bytes": 82872315136 + 34264189184, "batch": 1 << 20, "digest": "c4acca0c4152fa37",
+                  "sources": ["verify.cuh", "ops.cuh", "ec.cuh", "fp.cuh", "inv.cuh", "ptx.cuh",
+                              "curves_gen.cuh", "internal.h", "k_verify.cu"]}
 
 
 def verify_traffic(n):

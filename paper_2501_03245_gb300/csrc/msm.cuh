@@ -233,11 +233,12 @@ ECC_DEV uint32_t bucket_of(const uint32_t* off, uint32_t lo, uint32_t n, uint32_
 // keeps them in registers for finish, so no denominator array is written; the
 // 12-limb fields have no registers to spare and store the denominator in
 // compress instead.
-// A thread's items are BLOCK chunks apart.  Each pass issues the first-level
-// loads of the thread's next item (its sorted entry, its chunk's current
-// bucket and, for 8-limb fields in compress, x of its running sum) before the
-// current item's arithmetic, so the dependent loads behind them (the base
-// gather, the bucket offsets) start as soon as the next item begins.
+// A thread's items are BLOCK chunks apart.  Compress (and, for 8-limb fields,
+// DCWPA) issues the first-level loads of the thread's next item (its sorted
+// entry, its chunk's current bucket and, for 8-limb fields in compress, x of
+// its running sum) before the current item's arithmetic, so the dependent
+// loads behind them (the base gather, the bucket offsets) start as soon as the
+// next item begins.
 template <class C, int BLOCK>
 struct AccRound {
   using F = typename C::Fp;
