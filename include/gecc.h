@@ -134,6 +134,22 @@ int ecc_point_add_batch(ecc_curve_t curve, size_t n, const uint32_t* p, const ui
 int ecc_point_dbl_batch(ecc_curve_t curve, size_t n, const uint32_t* p, uint32_t* out,
                         void* stream);
 
+/* Batched affine PADD / PDBL (Section 3.3, Eqn 2-3) on a curve given at run
+ * time: y^2 = x^3 + a x + b over F_p, for an odd prime 5 <= p < 2^256 (the
+ * library's own curves have their constants compiled in; this entry point
+ * serves any other curve, tiny test curves included).
+ * prime, a: 8 little-endian limbs each, HOST memory, a < prime.  Primality of
+ * the prime is the caller's promise (not checked; a composite modulus gives
+ * meaningless results, but no fault).  b enters no formula, but must be nonzero
+ * mod p so that (0, 0), the encoding of O, is not a point of the curve.
+ * p, q, out: n points of 16 limbs (x then y, 8 canonical limbs each).
+ * dbl = 0: out[i] = p[i] + q[i]; dbl != 0: out[i] = 2 p[i] (q unused, may be
+ * NULL).  Points must be on the curve (not checked).  Errors: ECC_EINVAL for an
+ * even prime, a prime below 5, a >= prime, NULL or misaligned pointers,
+ * n > 2^30. */
+int ecc_point_op_custom(const uint32_t* prime, const uint32_t* a, size_t n, const uint32_t* p,
+                        const uint32_t* q, uint32_t* out, int dbl, void* stream);
+
 /* ---------------------------------------------------------------- ECDSA
  * Batched ECDSA verification (Section 5.2; SEC 1 section 4.1.4).
  * curve: ECC_SECP256K1, ECC_P256 or ECC_SM2 (others: ECC_EUNSUPPORTED).

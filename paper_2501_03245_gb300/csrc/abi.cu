@@ -246,6 +246,36 @@ int ecc_point_dbl_batch(ecc_curve_t curve, size_t n, const uint32_t* p, uint32_t
   return point_op("ecc_point_dbl_batch", curve, n, p, nullptr, out, 1, stream);
 }
 
+int ecc_point_op_custom(const uint32_t* prime, const uint32_t* a, size_t n, const uint32_t* p,
+                        const uint32_t* q, uint32_t* out, int dbl, void* stream) {
+  const char* name = "ecc_point_op_custom";
+  if (!prime || !a) return fail(ECC_EINVAL, "%s: NULL curve parameter", name);
+  if (!host_memory(prime) || !host_memory(a))
+    return fail(ECC_EINVAL, "%s: prime and a must be host memory", name);
+  CustomConsts cc;
+  switch (custom_consts(prime, a, &cc)) {
+    case 0: break;
+    case 1: return fail(ECC_EINVAL, "%s: the prime must be odd", name);
+    case 2: return fail(ECC_EINVAL, "%s: the prime must be at least 5", name);
+    default: return fail(ECC_EINVAL, "%s: a must be below the prime", name);
+  }
+  if (n == 0) return ok();
+  if (!p || !out || (!dbl && !q)) return fail(ECC_EINVAL, "%s: NULL pointer", name);
+  if (!aligned4(p) || !aligned4(out) || (q && !aligned4(q)))
+    return fail(ECC_EINVAL, "%s: pointers must be 4-byte aligned", name);
+  if (n > (size_t)1 << 30) return fail(ECC_EINVAL, "%s: n > 2^30", name);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t bytes = n * 16 * 4;
+  Arg P(p, bytes), Q(q ? q : p, bytes), O(out, bytes);
+  std::vector<Arg*> ins{&P};
+  if (!dbl) ins.push_back(&Q);
+  return with_args(name, st, ins, {&O}, [&]() {
+    return launch_point_add_custom(cc, n, static_cast<const uint32_t*>(P.dev),
+                                   static_cast<const uint32_t*>(Q.dev), static_cast<uint32_t*>(O.dev),
+                                   dbl, st);
+  });
+}
+
 int ecc_verify_batch(ecc_curve_t curve, size_t n, const uint8_t* hash, const uint8_t* r,
                      const uint8_t* s, const uint8_t* pubkey, uint8_t* ok_out, void* stream) {
   const char* name = "ecc_verify_batch";

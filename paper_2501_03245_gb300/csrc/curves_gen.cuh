@@ -13,6 +13,8 @@ struct Secp256k1Fp {
   static constexpr uint32_t QINV = 0xd2253531u;
   static constexpr int FORM = 0;
   static constexpr uint64_t QINV62 = 0x27c7f6e22ddacacfull;  // q^-1 mod 2^62
+  ECC_DEV static constexpr uint32_t qinv() { return QINV; }
+  ECC_DEV static constexpr uint64_t qinv62() { return QINV62; }
   ECC_DEV static constexpr uint32_t p(int i) {
     switch (i) { case 0: return 0xfffffc2fu; case 1: return 0xfffffffeu; case 2: return 0xffffffffu; case 3: return 0xffffffffu; case 4: return 0xffffffffu; case 5: return 0xffffffffu; case 6: return 0xffffffffu; case 7: return 0xffffffffu; default: return 0u; }
   }
@@ -36,6 +38,8 @@ struct Secp256k1Fn {
   static constexpr uint32_t QINV = 0x5588b13fu;
   static constexpr int FORM = 0;
   static constexpr uint64_t QINV62 = 0x34f20099aa774ec1ull;  // q^-1 mod 2^62
+  ECC_DEV static constexpr uint32_t qinv() { return QINV; }
+  ECC_DEV static constexpr uint64_t qinv62() { return QINV62; }
   ECC_DEV static constexpr uint32_t p(int i) {
     switch (i) { case 0: return 0xd0364141u; case 1: return 0xbfd25e8cu; case 2: return 0xaf48a03bu; case 3: return 0xbaaedce6u; case 4: return 0xfffffffeu; case 5: return 0xffffffffu; case 6: return 0xffffffffu; case 7: return 0xffffffffu; default: return 0u; }
   }
@@ -81,6 +85,8 @@ struct P256Fp {
   static constexpr uint32_t QINV = 0x00000001u;
   static constexpr int FORM = 0;
   static constexpr uint64_t QINV62 = 0x3fffffffffffffffull;  // q^-1 mod 2^62
+  ECC_DEV static constexpr uint32_t qinv() { return QINV; }
+  ECC_DEV static constexpr uint64_t qinv62() { return QINV62; }
   ECC_DEV static constexpr uint32_t p(int i) {
     switch (i) { case 0: return 0xffffffffu; case 1: return 0xffffffffu; case 2: return 0xffffffffu; case 3: return 0x00000000u; case 4: return 0x00000000u; case 5: return 0x00000000u; case 6: return 0x00000001u; case 7: return 0xffffffffu; default: return 0u; }
   }
@@ -108,6 +114,8 @@ struct P256Fn {
   static constexpr uint32_t QINV = 0xee00bc4fu;
   static constexpr int FORM = 0;
   static constexpr uint64_t QINV62 = 0x332e375511ff43b1ull;  // q^-1 mod 2^62
+  ECC_DEV static constexpr uint32_t qinv() { return QINV; }
+  ECC_DEV static constexpr uint64_t qinv62() { return QINV62; }
   ECC_DEV static constexpr uint32_t p(int i) {
     switch (i) { case 0: return 0xfc632551u; case 1: return 0xf3b9cac2u; case 2: return 0xa7179e84u; case 3: return 0xbce6faadu; case 4: return 0xffffffffu; case 5: return 0xffffffffu; case 6: return 0x00000000u; case 7: return 0xffffffffu; default: return 0u; }
   }
@@ -153,6 +161,8 @@ struct BN254Fp {
   static constexpr uint32_t QINV = 0xe4866389u;
   static constexpr int FORM = 0;
   static constexpr uint64_t QINV62 = 0x382df87d1b799c77ull;  // q^-1 mod 2^62
+  ECC_DEV static constexpr uint32_t qinv() { return QINV; }
+  ECC_DEV static constexpr uint64_t qinv62() { return QINV62; }
   ECC_DEV static constexpr uint32_t p(int i) {
     switch (i) { case 0: return 0xd87cfd47u; case 1: return 0x3c208c16u; case 2: return 0x6871ca8du; case 3: return 0x97816a91u; case 4: return 0x8181585du; case 5: return 0xb85045b6u; case 6: return 0xe131a029u; case 7: return 0x30644e72u; default: return 0u; }
   }
@@ -176,6 +186,8 @@ struct BN254Fn {
   static constexpr uint32_t QINV = 0xefffffffu;
   static constexpr int FORM = 0;
   static constexpr uint64_t QINV62 = 0x3d1e0a6c10000001ull;  // q^-1 mod 2^62
+  ECC_DEV static constexpr uint32_t qinv() { return QINV; }
+  ECC_DEV static constexpr uint64_t qinv62() { return QINV62; }
   ECC_DEV static constexpr uint32_t p(int i) {
     switch (i) { case 0: return 0xf0000001u; case 1: return 0x43e1f593u; case 2: return 0x79b97091u; case 3: return 0x2833e848u; case 4: return 0x8181585du; case 5: return 0xb85045b6u; case 6: return 0xe131a029u; case 7: return 0x30644e72u; default: return 0u; }
   }
@@ -221,6 +233,8 @@ struct BLS12_381Fp {
   static constexpr uint32_t QINV = 0xfffcfffdu;
   static constexpr int FORM = 0;
   static constexpr uint64_t QINV62 = 0x360c000300030003ull;  // q^-1 mod 2^62
+  ECC_DEV static constexpr uint32_t qinv() { return QINV; }
+  ECC_DEV static constexpr uint64_t qinv62() { return QINV62; }
   ECC_DEV static constexpr uint32_t p(int i) {
     switch (i) { case 0: return 0xffffaaabu; case 1: return 0xb9feffffu; case 2: return 0xb153ffffu; case 3: return 0x1eabfffeu; case 4: return 0xf6b0f624u; case 5: return 0x6730d2a0u; case 6: return 0xf38512bfu; case 7: return 0x64774b84u; case 8: return 0x434bacd7u; case 9: return 0x4b1ba7b6u; case 10: return 0x397fe69au; case 11: return 0x1a0111eau; default: return 0u; }
   }
@@ -244,6 +258,8 @@ struct BLS12_381Fn {
   static constexpr uint32_t QINV = 0xffffffffu;
   static constexpr int FORM = 0;
   static constexpr uint64_t QINV62 = 0x0000000100000001ull;  // q^-1 mod 2^62
+  ECC_DEV static constexpr uint32_t qinv() { return QINV; }
+  ECC_DEV static constexpr uint64_t qinv62() { return QINV62; }
   ECC_DEV static constexpr uint32_t p(int i) {
     switch (i) { case 0: return 0x00000001u; case 1: return 0xffffffffu; case 2: return 0xfffe5bfeu; case 3: return 0x53bda402u; case 4: return 0x09a1d805u; case 5: return 0x3339d808u; case 6: return 0x299d7d48u; case 7: return 0x73eda753u; default: return 0u; }
   }
@@ -289,6 +305,8 @@ struct SM2Fp {
   static constexpr uint32_t QINV = 0x00000001u;
   static constexpr int FORM = 0;
   static constexpr uint64_t QINV62 = 0x3fffffffffffffffull;  // q^-1 mod 2^62
+  ECC_DEV static constexpr uint32_t qinv() { return QINV; }
+  ECC_DEV static constexpr uint64_t qinv62() { return QINV62; }
   ECC_DEV static constexpr uint32_t p(int i) {
     switch (i) { case 0: return 0xffffffffu; case 1: return 0xffffffffu; case 2: return 0x00000000u; case 3: return 0xffffffffu; case 4: return 0xffffffffu; case 5: return 0xffffffffu; case 6: return 0xffffffffu; case 7: return 0xfffffffeu; default: return 0u; }
   }
@@ -312,6 +330,8 @@ struct SM2Fn {
   static constexpr uint32_t QINV = 0x72350975u;
   static constexpr int FORM = 0;
   static constexpr uint64_t QINV62 = 0x0d8061778dcaf68bull;  // q^-1 mod 2^62
+  ECC_DEV static constexpr uint32_t qinv() { return QINV; }
+  ECC_DEV static constexpr uint64_t qinv62() { return QINV62; }
   ECC_DEV static constexpr uint32_t p(int i) {
     switch (i) { case 0: return 0x39d54123u; case 1: return 0x53bbf409u; case 2: return 0x21c6052bu; case 3: return 0x7203df6bu; case 4: return 0xffffffffu; case 5: return 0xffffffffu; case 6: return 0xffffffffu; case 7: return 0xfffffffeu; default: return 0u; }
   }

@@ -3,7 +3,8 @@
 // Elements are N little-endian 32-bit limbs (N even: 8 for 254/256-bit fields,
 // 12 for the 381-bit field) held in registers, in Montgomery form a*R mod q with
 // R = 2^(32N), canonical in [0, q).  A field is a traits class F with
-//   N, QINV = -q^-1 mod 2^32, FORM (0 generic, 1 the P-256 prime), p(i),
+//   N, qinv() = -q^-1 mod 2^32, qinv62() = q^-1 mod 2^62, FORM (0 generic,
+//   1 the P-256 prime), p(i),
 //   r2(i) = R^2 mod q, one(i) = R mod q, pm2(i) = q - 2.
 //
 // mont_mul is Montgomery multiplication (Algorithm 2) with the operand-scanning
@@ -218,7 +219,7 @@ ECC_DEV void mont_mul(uint32_t* r, const uint32_t* a, const uint32_t* b) {
       continue;
     }
     // reduction row: u = T_0 * QINV, T += u * q (even and odd chains)
-    const uint32_t u = c[0] * F::QINV;
+    const uint32_t u = c[0] * F::qinv();
     c[0] = ptx::mad_lo_cc(u, F::p(0), c[0]);
     c[1] = ptx::madc_hi_cc(u, F::p(0), c[1]);
 #pragma unroll
@@ -311,7 +312,7 @@ __device__ __noinline__ void fe_inv_mont(uint32_t* r, const uint32_t* a) {
     q[i] = F::p(i);
     r3[i] = F::r3(i);
   }
-  inv_divsteps<L>(x, a, q, N, F::QINV62);
+  inv_divsteps<L>(x, a, q, N, F::qinv62());
   mont_mul<F>(r, x, r3);
 }
 

@@ -73,6 +73,8 @@ def field(name, q):
     s += f"  static constexpr uint32_t QINV = 0x{qinv:08x}u;\n"
     s += "  static constexpr int FORM = 0;\n"
     s += f"  static constexpr uint64_t QINV62 = 0x{pow(q, -1, 1 << 62):016x}ull;  // q^-1 mod 2^62\n"
+    s += "  ECC_DEV static constexpr uint32_t qinv() { return QINV; }\n"
+    s += "  ECC_DEV static constexpr uint64_t qinv62() { return QINV62; }\n"
     s += arr("p", q, n) + arr("r2", R * R % q, n) + arr("one", R % q, n) + arr("pm2", q - 2, n)
     s += arr("r3", R * R * R % q, n)
     s += "};\n\n"

@@ -51,6 +51,17 @@ cudaError_t launch_fe_inv_batch_noalloc(int curve, int field, size_t n, const ui
 // EC operators
 cudaError_t launch_point_add(int curve, size_t n, const uint32_t* p, const uint32_t* q,
                              uint32_t* out, int dbl, cudaStream_t st);
+// Curve supplied at run time (k_custom.cu): the 8-limb Montgomery constants of
+// an odd prime p < 2^256 and the curve's a in Montgomery form.
+struct CustomConsts {
+  uint32_t p[8], r2[8], one[8], pm2[8], r3[8], a[8];
+  uint32_t qinv, pad;
+  uint64_t qinv62;
+};
+// 0 on success; 1 p even, 2 p < 5, 3 a >= p.
+int custom_consts(const uint32_t* p, const uint32_t* a, CustomConsts* cc);
+cudaError_t launch_point_add_custom(const CustomConsts& cc, size_t n, const uint32_t* p,
+                                    const uint32_t* q, uint32_t* out, int dbl, cudaStream_t st);
 // Fixed-base table of a curve on the current device (built on first use,
 // synchronously on `st`): 32 x 256 entries, entry j*256+v = v 2^(8j) G, SoA
 // Montgomery (x block then y block).

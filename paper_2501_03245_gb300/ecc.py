@@ -42,6 +42,8 @@ _SIGS = {
                                  [ctypes.c_void_p] * 3),
     "ecc_point_add_batch": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t] + [ctypes.c_void_p] * 4),
     "ecc_point_dbl_batch": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t] + [ctypes.c_void_p] * 3),
+    "ecc_point_op_custom": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t] +
+                            [ctypes.c_void_p] * 3 + [ctypes.c_int, ctypes.c_void_p]),
     "ecc_verify_batch": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t] + [ctypes.c_void_p] * 6),
     "ecc_fixed_base_mul": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t] + [ctypes.c_void_p] * 3),
     "ecc_sign_batch": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t] + [ctypes.c_void_p] * 7),
@@ -167,6 +169,18 @@ def ecc_point_add_batch(curve, n, p, q, out, stream=None):
 
 def ecc_point_dbl_batch(curve, n, p, out, stream=None):
     return _check(load().ecc_point_dbl_batch(curve, n, _ptr(p), _ptr(out), _stream(stream)))
+
+
+def ecc_point_op_custom(prime, a, n, p, q, out, dbl=0, stream=None):
+    """prime, a: Python ints (converted to 8 host limbs each)."""
+    import numpy as np
+
+    def limbs(v):
+        return np.array([(v >> (32 * i)) & 0xFFFFFFFF for i in range(8)], dtype=np.uint32)
+
+    pl, al = limbs(prime), limbs(a)
+    return _check(load().ecc_point_op_custom(pl.ctypes.data, al.ctypes.data, n, _ptr(p), _ptr(q),
+                                             _ptr(out), int(dbl), _stream(stream)))
 
 
 def ecc_verify_batch(curve, n, hash, r, s, pubkey, ok_out, stream=None):
