@@ -5,8 +5,10 @@ budget set at start-up, loops that cannot take the synchronisation cudaMalloc
 implies, hosts without an allocator).  This entry point keeps its scratch in a
 fixed device array inside the library.  The test calls it through the C ABI and
 checks, on two calls in a row, that it returns exactly what ecc_fp_inv_batch
-returns for the same input (exact integers: the tolerance is zero).  It runs last
-so that a failure here leaves every other test already run.
+returns for the same input and what the oracle's inverse x^-1 mod q gives for
+every element (exact integers: the tolerance is zero), in a base field and a
+scalar field.  It runs last so that a failure here leaves every other test
+already run.
 """
 import numpy as np
 import pytest
@@ -17,14 +19,18 @@ pytestmark = pytest.mark.gpu
 
 P256_P = 0xFFFFFFFF00000001000000000000000000000000FFFFFFFFFFFFFFFFFFFFFFFF
 BLS_P = 0x1A0111EA397FE69A4B1BA7B6434BACD764774B84F38512BF6730D2A0F6B0F6241EABFFFEB153FFFFB9FEFFFFFFFFAAAB
+BN_R = 0x30644E72E131A029B85045B68181585D2833E84879B9709143E1F593F0000001
 
 
 @pytest.mark.parametrize("curve,field,modulus,limbs,n", [
     (1, 0, P256_P, 8, 65536),     # the maximum size
     (3, 0, BLS_P, 12, 5000),
-], ids=["P-256-max", "BLS12-381"])
+    (2, 1, BN_R, 8, 65536),       # a scalar field (BN254 r), the maximum size
+], ids=["P-256-max", "BLS12-381", "BN254-Fr-max"])
 def test_noalloc_matches_allocating_entry_point(gpu_lib, curve, field, modulus, limbs, n):
     import torch
+
+    from oracle import field as ofield
 
     for call in range(2):  # two calls in a row share the same scratch
         vals = synth.uniform_limbs(0x6ECC9000 + 10 * call + curve, 1, n, modulus, nlimbs=limbs)
@@ -36,6 +42,9 @@ def test_noalloc_matches_allocating_entry_point(gpu_lib, curve, field, modulus, 
         gpu_lib.ecc_fp_inv_batch_noalloc(curve, field, n, a, got)
         torch.cuda.synchronize()
         assert torch.equal(got, want), call
+        xs = synth.limbs_to_ints(vals)
+        inv = synth.limbs_to_ints(got.cpu().numpy().view(np.uint32))
+        assert inv == [ofield.inv(modulus, x) for x in xs], call
 
 
 def test_noalloc_rejects_oversize_and_host_buffers(gpu_lib):
