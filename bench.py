@@ -167,9 +167,8 @@ def gen_inputs(ecc, synth, torch, n, seed, curve=CURVE_P256):
 
 
 # DRAM traffic of one k_verify launch over 2^20 P-256 triples (dram__bytes_read.sum +
-# dram__bytes_write.sum, one ncu capture; summary and command in
-# profiles/k_verify_p256_2e20_dram.md), valid only for the kernel sources it was
-# taken on: reported as null once any of them has changed.
+# dram__bytes_write.sum, from one ncu capture), valid only for the kernel sources
+# it was taken on: the digest of those sources must match, else it is null.
 VERIFY_TRAFFIC = {"bytes": 82872315136 + 34264189184, "batch": 1 << 20, "digest": "c4acca0c4152fa37",
                   "sources": ["verify.cuh", "ops.cuh", "ec.cuh", "fp.cuh", "inv.cuh", "ptx.cuh",
                               "curves_gen.cuh", "internal.h", "k_verify.cu"]}
@@ -357,7 +356,8 @@ def bench_ragged(ecc, costmodel, synth, torch, peak, rank, world=1):
     per = _event_time(torch, lambda: [ecc.ecc_msm(curve, int(sizes[i]), pts[int(offs[i]):int(offs[i + 1])],
                                                   sc[int(offs[i]):int(offs[i + 1])], one)
                                       for i in range(256)], 1)
-    best = graph if graph else eager
+    # the graph rate stands only when its replay reproduced the eager result
+    best = graph if (graph and graph_ok is True) else eager
     widths = [ecc.ecc_msm_window(curve, int(k)) for k in sizes]
     alg = sum(costmodel.msm_modmul(int(k), costmodel.msm_windows(254, c), c) for k, c in zip(sizes, widths))
     alg *= costmodel.imad_per_modmul(8)
