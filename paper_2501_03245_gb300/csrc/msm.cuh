@@ -121,10 +121,13 @@ __global__ void k_msm_count(const MsmInst* inst, int num, const uint32_t* __rest
 
 // Entries are written chunk-transposed: entry p goes to [p % CH][p / CH].  Only
 // the point index is stored; the bucket of position p follows from the offsets.
+// The bucket of each chunk's first entry is recorded in cur (the accumulation's
+// per-chunk bucket cursor starts there).
 template <class C>
 __global__ void k_msm_scatter(const MsmInst* inst, int num, const uint32_t* __restrict__ scalars,
                               uint64_t total, uint32_t* __restrict__ cursor,
-                              uint32_t* __restrict__ vals, uint64_t n_chunks) {
+                              uint32_t* __restrict__ vals, uint64_t n_chunks,
+                              uint32_t* __restrict__ cur) {
   const uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (g >= total) return;
   const MsmInst in = inst[find_inst(inst, num, g)];
@@ -140,6 +143,7 @@ __global__ void k_msm_scatter(const MsmInst* inst, int num, const uint32_t* __re
     const uint32_t p = atomicAdd(cursor + b, 1u);
     const uint32_t idx = (uint32_t)(pidx + (uint64_t)w * in.pre_stride);  // < 2^31 (host check)
     vals[(uint64_t)(p % kAccChunk) * n_chunks + p / kAccChunk] = idx | (d < 0 ? 0x80000000u : 0u);
+    if (p % kAccChunk == 0) cur[p / kAccChunk] = b;
   });
 }
 
@@ -224,88 +228,247 @@ ECC_DEV uint32_t bucket_of(const uint32_t* off, uint32_t lo, uint32_t n, uint32_
   return lo;
 }
 
-// One round of the chunked running sums: entry j of every chunk is added to
-// the chunk's running sum S (or starts a new one at a bucket boundary).
-// Compress (den_c) loads only x of S and of the base, as the compress step of
-// Section 3.3 does; y is needed only when an operand may be O (x = 0) or the
-// x coordinates agree (doubling or P = -T), which random inputs almost never
-// hit.  For 8-limb fields the DCWPA step (den_d) loads both operands once and
-// keeps them in registers for finish, so no denominator array is written; the
-// 12-limb fields have no registers to spare and store the denominator in
-// compress instead.
-// A thread's items are BLOCK chunks apart.  Compress (and, for 8-limb fields,
-// DCWPA) issues the first-level loads of the thread's next item (its sorted
-// entry, its chunk's current bucket and, for 8-limb fields in compress, x of
-// its running sum) before the current item's arithmetic, so the dependent
-// loads behind them (the base gather, the bucket offsets) start as soon as the
-// next item begins.
+// Entry j of chunk c: whether it exists, its bucket, and whether it starts a
+// new running sum.  pb = the chunk's bucket before this entry (for j = 0 the
+// bucket of the entry itself, recorded by the scatter); off1 = off[pb + 1],
+// the end of that bucket (unused for j = 0).
+struct AccCls {
+  bool live, start;
+  uint32_t bucket, prev;
+};
+
+template <class C>
+ECC_DEV AccCls acc_classify(const AccArgs<C>& a, uint64_t c, int j, uint32_t entries, uint32_t pb,
+                            uint32_t off1) {
+  AccCls k{false, false, pb, pb};
+  const uint32_t p = (uint32_t)(c * kAccChunk + j);
+  if (p >= entries) return k;
+  k.live = true;
+  if (j == 0 || p >= off1) k.start = true;
+  if (j == 0 || p < off1) return k;
+  k.bucket = pb + 1;  // usually the next bucket; skip empty ones otherwise
+  if (a.off[k.bucket + 1] <= p) k.bucket = bucket_of(a.off, k.bucket + 1, a.n_buckets, p);
+  return k;
+}
+
+// ---- 8-limb fields: one round with every operand staged in shared memory.
+// Entry j of every chunk is added to the chunk's running sum S (or starts a
+// new one at a bucket boundary).  Each thread owns kStageVecs 16-byte vectors of
+// shared memory (layout [vector][thread], so a warp's copies of one vector are
+// 512 contiguous bytes) after the GAS scratch.  While a thread computes on its
+// item k, the cp.async copies of item k+1's operands and the first-level loads
+// of item k+2 (its sorted entry and its chunk's bucket cursor) are in flight,
+// and so is item k+1's bucket end off[pb + 1]: the gathers behind the sorted
+// entries never stall the arithmetic.  Compress stages only x of S and of the
+// base (the compress step of Section 3.3); y is read, directly, only when an
+// operand may be O (x = 0) or the two x agree (doubling or P = -T), which
+// random inputs almost never hit.  DCWPA stages S, the base and the prefix
+// product, and keeps the operands in registers through the finish, so no
+// denominator array exists.
+constexpr int kStageVecs = 10;  // S.x 0-1, S.y 2-3, base.x 4-5, base.y 6-7, prefix 8-9
+
+template <int BLOCK>
+struct Stage {
+  uint4* v;  // [kStageVecs][BLOCK]
+  ECC_DEV uint4* at(int k) const { return v + k * BLOCK + threadIdx.x; }
+  // vectors k0, k0 + 1 -> 8 words
+  ECC_DEV void get(int k0, uint32_t* r) const {
+    const uint4 p = *at(k0), q = *at(k0 + 1);
+    r[0] = p.x; r[1] = p.y; r[2] = p.z; r[3] = p.w;
+    r[4] = q.x; r[5] = q.y; r[6] = q.z; r[7] = q.w;
+  }
+};
+
+// Issues the copies of chunk c's operands (entry v): x of S and of the base,
+// and with `full` also y of both and the prefix product.  The base is touched
+// only for an existing entry (v is meaningful only then).
+template <class C, int BLOCK>
+ECC_DEV void acc_stage(const Stage<BLOCK>& sg, const AccArgs<C>& a, uint64_t c, uint32_t v, bool live,
+                       bool full) {
+  const SoA<typename C::Fp>& sx = a.S.x;
+  ptx::cp_async16(sg.at(0), sx.vec + c);
+  ptx::cp_async16(sg.at(1), sx.vec + sx.stride + c);
+  if (full) {
+    const SoA<typename C::Fp>& sy = a.S.y;
+    ptx::cp_async16(sg.at(2), sy.vec + c);
+    ptx::cp_async16(sg.at(3), sy.vec + sy.stride + c);
+    ptx::cp_async16(sg.at(8), a.M.vec + c);
+    ptx::cp_async16(sg.at(9), a.M.vec + a.M.stride + c);
+  }
+  if (live) {
+    const uint4* p = base_ptr(a, v);
+    ptx::cp_async16(sg.at(4), p);
+    ptx::cp_async16(sg.at(5), p + 1);
+    if (full) {
+      ptx::cp_async16(sg.at(6), p + 2);
+      ptx::cp_async16(sg.at(7), p + 3);
+    }
+  }
+  ptx::cp_async_commit();
+}
+
+template <class C, int BLOCK>
+__device__ void acc_round_staged(const AccArgs<C>& a, int j, uint32_t entries, uint64_t begin,
+                                 uint64_t end, const Stage<BLOCK>& sg, GasSmem<8, BLOCK>& sm) {
+  using F = typename C::Fp;
+  constexpr int N = 8;
+  static_assert(F::N == N, "8-limb fields only");
+  const uint64_t i0 = begin + threadIdx.x;
+  const uint64_t row = (uint64_t)j * a.n_chunks;
+  auto is_live = [&](uint64_t c) { return (uint32_t)(c * kAccChunk + j) < entries; };
+  // pipeline registers: item k (v0, pb0, o0), item k+1 (v1, pb1), item k+2 (v2, pb2)
+  uint32_t v0 = 0, pb0 = 0, o0 = 0, v1 = 0, pb1 = 0;
+  // ---- compress, ascending
+  uint32_t run[N];
+  fe_set_one<F>(run);
+  if (i0 < end) {
+    v0 = a.vals[row + i0];
+    pb0 = a.cur[i0];
+    acc_stage<C, BLOCK>(sg, a, i0, v0, is_live(i0), false);
+    if (j > 0) o0 = a.off[pb0 + 1];
+    if (i0 + BLOCK < end) {
+      v1 = a.vals[row + i0 + BLOCK];
+      pb1 = a.cur[i0 + BLOCK];
+    }
+  }
+  for (uint64_t c = i0; c < end; c += BLOCK) {
+    ptx::cp_async_wait_all();
+    uint32_t x1[N], x2[N];
+    sg.get(0, x1);
+    sg.get(4, x2);
+    const uint64_t cn = c + BLOCK;
+    uint32_t o1 = 0, v2 = 0, pb2 = 0;
+    if (cn < end) {
+      acc_stage<C, BLOCK>(sg, a, cn, v1, is_live(cn), false);
+      if (j > 0) o1 = a.off[pb1 + 1];
+      if (cn + BLOCK < end) {
+        v2 = a.vals[row + cn + BLOCK];
+        pb2 = a.cur[cn + BLOCK];
+      }
+    }
+    a.M.store(c, run);
+    const AccCls k = acc_classify(a, c, j, entries, pb0, o0);
+    uint32_t d[N];
+    if (!k.live || k.start) {
+      fe_set_one<F>(d);
+    } else if (fe_is_zero<F>(x1) || fe_is_zero<F>(x2) || fe_eq<F>(x1, x2)) {
+      uint32_t y1[N], y2[N];
+      a.S.y.load(c, y1);
+      load_base_y<C>(a, v0, y2);
+      add_den<C>(d, x1, y1, x2, y2);
+    } else {
+      fe_sub<F>(d, x2, x1);
+    }
+    mont_mul<F>(run, run, d);
+    v0 = v1; pb0 = pb1; o0 = o1;
+    v1 = v2; pb1 = pb2;
+  }
+  // ---- inverse of the CTA's product (GAS, Section 3.2)
+  uint32_t inv[N];
+  cta_invert<F, BLOCK>(inv, run, sm);
+  if (i0 >= end) return;
+  // ---- DCWPA, descending
+  const uint64_t last = i0 + ((end - 1 - i0) / BLOCK) * BLOCK;
+  v0 = a.vals[row + last];
+  pb0 = a.cur[last];
+  acc_stage<C, BLOCK>(sg, a, last, v0, is_live(last), true);
+  o0 = j > 0 ? a.off[pb0 + 1] : 0u;
+  if (last >= i0 + BLOCK) {
+    v1 = a.vals[row + last - BLOCK];
+    pb1 = a.cur[last - BLOCK];
+  }
+  for (uint64_t c = last;; c -= BLOCK) {
+    ptx::cp_async_wait_all();
+    uint32_t xs[N], ys[N], xp[N], yp[N], pre[N];
+    sg.get(0, xs);
+    sg.get(2, ys);
+    sg.get(4, xp);
+    sg.get(6, yp);
+    sg.get(8, pre);
+    const bool more = c >= i0 + BLOCK;
+    uint32_t o1 = 0, v2 = 0, pb2 = 0;
+    if (more) {
+      const uint64_t cn = c - BLOCK;
+      acc_stage<C, BLOCK>(sg, a, cn, v1, is_live(cn), true);
+      if (j > 0) o1 = a.off[pb1 + 1];
+      if (cn >= i0 + BLOCK) {
+        v2 = a.vals[row + cn - BLOCK];
+        pb2 = a.cur[cn - BLOCK];
+      }
+    }
+    const AccCls k = acc_classify(a, c, j, entries, pb0, o0);
+    if (v0 & 0x80000000u) fe_neg<F>(yp, yp);
+    uint32_t d[N];
+    int kind = ADD_RET_T;
+    if (!k.live || k.start) {
+      fe_set_one<F>(d);
+    } else {
+      kind = add_den<C>(d, xs, ys, xp, yp);
+    }
+    uint32_t mine[N];
+    mont_mul<F>(mine, inv, pre);
+    mont_mul<F>(inv, inv, d);
+    if (k.live) {
+      if (k.start) {
+        if (j > 0) {
+          a.partial.store(partial_slot(a, k.prev, c), xs, ys);
+          a.cur[c] = k.bucket;
+        }
+        a.S.store(c, xp, yp);
+      } else {
+        add_finish<C>(xs, ys, kind, mine, xs, ys, xp, yp);
+        a.S.store(c, xs, ys);
+      }
+    }
+    if (!more) break;
+    v0 = v1; pb0 = pb1; o0 = o1;
+    v1 = v2; pb1 = pb2;
+  }
+}
+
+// ---- 12-limb fields: the round as a batch_round client.  Compress loads only
+// x of S and of the base (y only when an operand may be O or the x agree) and
+// stores the round's denominator (holding the DCWPA operands in registers
+// would spill at 12 limbs); DCWPA reloads the denominator, finish the operands.
+// Compress issues the first-level loads of the thread's next item (its sorted
+// entry and its chunk's bucket cursor) one item ahead.
 template <class C, int BLOCK>
 struct AccRound {
   using F = typename C::Fp;
   static constexpr int N = F::N;
   static constexpr int OPS = 1;
-  static constexpr bool kHold = N <= 8;
   const AccArgs<C>* a;
   int j;
   uint32_t entries;
   uint64_t begin, end;  // this CTA's chunks
   uint64_t nc = ~0ull;  // chunk whose loads below were issued ahead
   uint32_t nv, ncur;
-  uint32_t nxs[kHold ? N : 1];
-  uint32_t bucket, prev, cv;
-  bool start, live;
-  int kind;
-  uint32_t xs[kHold ? N : 1], ys[kHold ? N : 1], xp[kHold ? N : 1], yp[kHold ? N : 1];
-  // first-level loads of chunk c: entry j and (j > 0) the chunk's current bucket
   ECC_DEV void fetch(uint64_t c, uint32_t& v, uint32_t& pb) const {
     v = a->vals[(uint64_t)j * a->n_chunks + c];
-    pb = j > 0 ? a->cur[c] : 0u;
+    pb = a->cur[c];
   }
-  ECC_DEV void ahead(uint64_t c, bool with_x) {
-    nc = c;
-    fetch(c, nv, ncur);
-    if constexpr (kHold) {
-      if (with_x) a->S.x.load(c, nxs);
-    }
-  }
-  // Entry j of chunk c: its bucket, and whether it starts a new running sum
-  // (pb = the chunk's bucket before this entry).
-  ECC_DEV void classify(uint64_t c, uint32_t pb) {
-    const uint32_t p = (uint32_t)(c * kAccChunk + j);
-    live = p < entries;
-    if (!live) return;
-    if (j == 0) {
-      bucket = bucket_of(a->off, 0, a->n_buckets, p);
-      start = true;
-      return;
-    }
-    prev = pb;
-    if (p < a->off[prev + 1]) {
-      bucket = prev;
-      start = false;
-      return;
-    }
-    start = true;
-    bucket = prev + 1;  // usually the next bucket; skip empty ones otherwise
-    if (a->off[bucket + 1] <= p) bucket = bucket_of(a->off, bucket + 1, a->n_buckets, p);
+  ECC_DEV AccCls classify(uint64_t c, uint32_t pb) const {
+    const bool need = j > 0 && (uint32_t)(c * kAccChunk + j) < entries;
+    return acc_classify(*a, c, j, entries, pb, need ? a->off[pb + 1] : 0u);
   }
   ECC_DEV void den_c(size_t c, int, uint32_t* d) {
-    uint32_t v, pb, x1[N];
+    uint32_t v, pb;
     if (nc == c) {
       v = nv;
       pb = ncur;
-      if constexpr (kHold) fe_copy<F>(x1, nxs);
     } else {
       fetch(c, v, pb);
-      if constexpr (kHold) a->S.x.load(c, x1);
     }
-    if (c + BLOCK < end) ahead(c + BLOCK, true);
-    classify(c, pb);
-    if (!live || start) {
+    if (c + BLOCK < end) {
+      nc = c + BLOCK;
+      fetch(nc, nv, ncur);
+    }
+    const AccCls k = classify(c, pb);
+    if (!k.live || k.start) {
       fe_set_one<F>(d);
     } else {
-      uint32_t x2[N];
-      if constexpr (!kHold) a->S.x.load(c, x1);
+      uint32_t x1[N], x2[N];
+      a->S.x.load(c, x1);
       load_base_x<C>(*a, v, x2);
       if (fe_is_zero<F>(x1) || fe_is_zero<F>(x2) || fe_eq<F>(x1, x2)) {
         uint32_t y1[N], y2[N];
@@ -316,69 +479,41 @@ struct AccRound {
         fe_sub<F>(d, x2, x1);
       }
     }
-    if (!kHold) a->D.store(c, d);
+    a->D.store(c, d);
   }
-  ECC_DEV void den_d(size_t c, int, uint32_t* d) {
-    if constexpr (kHold) {
-      // DCWPA walks the items downwards
-      uint32_t pb;
-      if (nc == c) {
-        cv = nv;
-        pb = ncur;
-      } else {
-        fetch(c, cv, pb);
-      }
-      if (c >= begin + BLOCK) ahead(c - BLOCK, false);
-      classify(c, pb);
-      if (!live || start) {
-        fe_set_one<F>(d);
-      } else {
-        a->S.load(c, xs, ys);
-        load_base<C>(*a, cv, xp, yp);
-        kind = add_den<C>(d, xs, ys, xp, yp);
-      }
-    } else {
-      a->D.load(c, d);
-    }
-  }
+  ECC_DEV void den_d(size_t c, int, uint32_t* d) { a->D.load(c, d); }
   ECC_DEV void finish(size_t c, const uint32_t (*inv)[N]) {
-    if constexpr (kHold) {
-      if (!live) return;
-      if (start) {
-        load_base<C>(*a, cv, xp, yp);
-        if (j > 0) {
-          a->S.load(c, xs, ys);
-          a->partial.store(partial_slot(*a, prev, c), xs, ys);
-        }
-        a->S.store(c, xp, yp);
-        a->cur[c] = bucket;
-      } else {
-        add_finish<C>(xs, ys, kind, inv[0], xs, ys, xp, yp);
-        a->S.store(c, xs, ys);
-      }
-    } else {
-      uint32_t v, pb;
-      fetch(c, v, pb);
-      classify(c, pb);
-      if (!live) return;
-      uint32_t x1[N], y1[N], x2[N], y2[N];
-      load_base<C>(*a, v, x2, y2);
-      if (start) {
-        if (j > 0) {
-          a->S.load(c, x1, y1);
-          a->partial.store(partial_slot(*a, prev, c), x1, y1);
-        }
-        a->S.store(c, x2, y2);
-        a->cur[c] = bucket;
-      } else {
+    uint32_t v, pb;
+    fetch(c, v, pb);
+    const AccCls k = classify(c, pb);
+    if (!k.live) return;
+    uint32_t x1[N], y1[N], x2[N], y2[N];
+    load_base<C>(*a, v, x2, y2);
+    if (k.start) {
+      if (j > 0) {
         a->S.load(c, x1, y1);
-        const int k = add_kind<C>(x1, y1, x2, y2);
-        add_finish<C>(x1, y1, k, inv[0], x1, y1, x2, y2);
-        a->S.store(c, x1, y1);
+        a->partial.store(partial_slot(*a, k.prev, c), x1, y1);
+        a->cur[c] = k.bucket;
       }
+      a->S.store(c, x2, y2);
+    } else {
+      a->S.load(c, x1, y1);
+      const int kind = add_kind<C>(x1, y1, x2, y2);
+      add_finish<C>(x1, y1, kind, inv[0], x1, y1, x2, y2);
+      a->S.store(c, x1, y1);
     }
   }
 };
+
+// Fields whose accumulation stages its operands in shared memory.
+template <class F>
+inline constexpr bool kAccStaged = F::N == 8;
+
+// Dynamic shared memory of k_msm_accumulate.
+template <int N, int BLOCK>
+__host__ __device__ constexpr size_t acc_smem_bytes() {
+  return sizeof(GasSmem<N, BLOCK>) + (N == 8 ? (size_t)kStageVecs * BLOCK * 16 : 0);
+}
 
 template <class C, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, kGasResidentThreads / BLOCK) k_msm_accumulate(AccArgs<C> a) {
@@ -391,9 +526,16 @@ __global__ void __launch_bounds__(BLOCK, kGasResidentThreads / BLOCK) k_msm_accu
   uint64_t end = begin + a.per_cta;
   if (end > used) end = used;
   if (end < begin) end = begin;
-  for (int j = 0; j < kAccChunk; ++j) {
-    AccRound<C, BLOCK> rd{&a, j, entries, begin, end};
-    batch_round<F, BLOCK>(rd, begin, end, a.M, sm);
+  if constexpr (kAccStaged<F>) {
+    static_assert(sizeof(GasSmem<N, BLOCK>) % 16 == 0, "staging area alignment");
+    const Stage<BLOCK> sg{reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(&sm) +
+                                                   sizeof(GasSmem<N, BLOCK>))};
+    for (int j = 0; j < kAccChunk; ++j) acc_round_staged<C, BLOCK>(a, j, entries, begin, end, sg, sm);
+  } else {
+    for (int j = 0; j < kAccChunk; ++j) {
+      AccRound<C, BLOCK> rd{&a, j, entries, begin, end};
+      batch_round<F, BLOCK>(rd, begin, end, a.M, sm);
+    }
   }
   // flush the last running sum of every chunk
   for (uint64_t c = begin + threadIdx.x; c < end; c += BLOCK) {

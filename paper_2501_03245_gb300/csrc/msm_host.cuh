@@ -53,7 +53,7 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
   const uint64_t sz_ops = up(n_part * 4);
   // per chunk: running sum (x, y), prefix product and, where the accumulation
   // does not keep its operands in registers, the round's denominator
-  constexpr bool kHold = AccRound<C, kAccBlock>::kHold;
+  constexpr bool kHold = kAccStaged<F>;
   constexpr uint64_t kChunkArrays = kHold ? 3 : 4;
   const uint64_t bytes = sz_inst + 5 * sz_b1 + sz_kv + sz_cur + kChunkArrays * sz_S + 3 * sz_P + sz_ops + 256;
   Scratch ws;
@@ -87,7 +87,8 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
   e = exclusive_scan(npart, B, poff, st);
   if (e != cudaSuccess) return e;
   if (L.total_points)
-    k_msm_scatter<C><<<pb, 256, 0, st>>>(d_inst, num, scalars, L.total_points, cursor, vals, NC);
+    k_msm_scatter<C><<<pb, 256, 0, st>>>(d_inst, num, scalars, L.total_points, cursor, vals, NC,
+                                          cur);
   // ---- 3: bucket accumulation (batched affine, one launch)
   AccArgs<C> a;
   a.vals = vals;
@@ -107,10 +108,11 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
   ctas = (NC + per - 1) / per;
   a.per_cta = per;
   const size_t smem = sizeof(GasSmem<N, kAccBlock>);
+  const size_t acc_smem = acc_smem_bytes<N, kAccBlock>();
   e = cudaFuncSetAttribute(k_msm_accumulate<C, kAccBlock>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)acc_smem);
   if (e != cudaSuccess) return e;
-  k_msm_accumulate<C, kAccBlock><<<(unsigned)ctas, kAccBlock, smem, st>>>(a);
+  k_msm_accumulate<C, kAccBlock><<<(unsigned)ctas, kAccBlock, acc_smem, st>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // ---- fold the partial sums of every bucket into its first slot

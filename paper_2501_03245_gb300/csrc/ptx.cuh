@@ -76,4 +76,15 @@ ECC_DEV uint32_t madc_hi(uint32_t a, uint32_t b, uint32_t c) {
   return r;
 }
 
+// Asynchronous 16-byte global -> shared copies (cp.async, cached in L2 only):
+// the data lands in shared memory without passing through registers, so a
+// thread can fetch its next item's operands while it computes on the current
+// one.  A thread reads back only what it copied itself, after wait_all.
+ECC_DEV void cp_async16(void* smem, const void* gmem) {
+  const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+ECC_DEV void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+ECC_DEV void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 }  // namespace ptx
