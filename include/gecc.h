@@ -77,9 +77,9 @@ int ecc_limbs(ecc_curve_t curve);
  * multiplication; inputs are converted into Montgomery form and back).
  * field: ECC_FIELD_BASE (q = p) or ECC_FIELD_SCALAR (q = group order n).
  * a, b, out: n rows of L limbs (L = ecc_limbs() for the base field, 8 for the
- * scalar field); inputs must be canonical.  On the P-256 base field these
- * unit operations reduce with the special form of the prime (Section 4.2); the
- * results are the same integers. */
+ * scalar field); inputs must be canonical.  On the P-256 and secp256k1 base
+ * fields these unit operations reduce with the special form of the prime
+ * (Section 4.2); the results are the same integers. */
 int ecc_fp_mul(ecc_curve_t curve, int field, size_t n, const uint32_t* a, const uint32_t* b,
                uint32_t* out, void* stream);
 
@@ -239,6 +239,18 @@ int ecc_msm_bases_ragged(void* handle, size_t num, const uint64_t* sizes, const 
 int ecc_msm_window(ecc_curve_t curve, size_t n);
 int ecc_msm_set_window(ecc_curve_t curve, int log2_n, int c);
 
+/* Bucket layout of the reduction (the autotuner's second knob): the bucket rows
+ * of an n-point MSM are cut into first-level chunks of 2^k consecutive buckets,
+ * each walked by running sums in k-dependent batched affine rounds (2^k + 1
+ * addition rounds and k doubling rounds, one CTA-wide inversion each) before
+ * the short Jacobian levels combine the chunks.  Smaller chunks mean fewer
+ * rounds and more chunks.  ecc_msm_reduce_chunk returns k for an n-point MSM
+ * (default 5, capped at c - 1); ecc_msm_set_reduce_chunk overrides it for the
+ * size class floor(log2 n) (log2_chunk 1..10; 0 restores the default).  Results
+ * do not depend on k. */
+int ecc_msm_reduce_chunk(ecc_curve_t curve, size_t n);
+int ecc_msm_set_reduce_chunk(ecc_curve_t curve, int log2_n, int log2_chunk);
+
 /* ---------------------------------------------------------------- benchmarks
  * Integer multiply-add issue-rate probe (the microbenchmark method of
  * Section 4.1, Table 2): each of `threads` threads runs `iters` iterations of
@@ -250,8 +262,10 @@ int ecc_bench_imad(size_t threads, int iters, uint32_t* sink, void* stream);
 /* Montgomery multiplications in registers: each thread runs `iters` rounds of
  * 4 independent mont_mul chains of the curve's base field.  reduction 0 = the
  * generic Montgomery reduction (Algorithm 2, as in every fused kernel);
- * 1 = the special-form reduction of Section 4.2 (P-256 only, ECC_EUNSUPPORTED
- * otherwise; the ecc_fp_* unit operations on the P-256 base field use it).
+ * 1 = the special-form reduction of Section 4.2 (P-256: u = T_0 and u q by
+ * additions; secp256k1: u q = u 2^256 - u (2^32 + 977), one product per row;
+ * ECC_EUNSUPPORTED on the other curves; the ecc_fp_* unit operations on these
+ * two base fields use it).
  * sink as above. */
 int ecc_bench_modmul(ecc_curve_t curve, int reduction, size_t threads, int iters, uint32_t* sink,
                      void* stream);

@@ -510,6 +510,21 @@ int ecc_msm_set_window(ecc_curve_t curve, int log2_n, int c) {
   return ok();
 }
 
+int ecc_msm_reduce_chunk(ecc_curve_t curve, size_t n) {
+  if (!valid_curve(curve)) return fail(ECC_EINVAL, "ecc_msm_reduce_chunk: unknown curve %d", (int)curve);
+  return msm_reduce_log(curve, n);
+}
+
+int ecc_msm_set_reduce_chunk(ecc_curve_t curve, int log2_n, int log2_chunk) {
+  if (!valid_curve(curve))
+    return fail(ECC_EINVAL, "ecc_msm_set_reduce_chunk: unknown curve %d", (int)curve);
+  if (log2_n < 0 || log2_n > 40 || log2_chunk < 0 || log2_chunk > kMsmReduceLogMax)
+    return fail(ECC_EINVAL, "ecc_msm_set_reduce_chunk: need 0 <= log2_n <= 40 and 0 <= log2_chunk <= %d",
+                kMsmReduceLogMax);
+  msm_set_reduce_log(curve, log2_n, log2_chunk);
+  return ok();
+}
+
 int ecc_bench_imad(size_t threads, int iters, uint32_t* sink, void* stream) {
   if (threads == 0 || iters < 0 || !sink) return fail(ECC_EINVAL, "ecc_bench_imad: bad argument");
   cudaError_t e = launch_bench_imad(threads, iters, sink, static_cast<cudaStream_t>(stream));
@@ -522,8 +537,9 @@ int ecc_bench_modmul(ecc_curve_t curve, int reduction, size_t threads, int iters
   if (!valid_curve(curve)) return fail(ECC_EINVAL, "ecc_bench_modmul: unknown curve");
   if (threads == 0 || iters < 0 || !sink || reduction < 0 || reduction > 1)
     return fail(ECC_EINVAL, "ecc_bench_modmul: bad argument");
-  if (reduction == 1 && curve != ECC_P256)
-    return fail(ECC_EUNSUPPORTED, "ecc_bench_modmul: the special-form reduction is P-256 only");
+  if (reduction == 1 && curve != ECC_P256 && curve != ECC_SECP256K1)
+    return fail(ECC_EUNSUPPORTED, "ecc_bench_modmul: the special-form reduction is offered for the "
+                "P-256 and secp256k1 primes");
   cudaError_t e = launch_bench_modmul(curve, reduction, threads, iters, sink,
                                       static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "ecc_bench_modmul");

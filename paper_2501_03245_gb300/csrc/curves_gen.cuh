@@ -32,6 +32,10 @@ struct Secp256k1Fp {
   }
 };
 
+struct Secp256k1FpSpecial : Secp256k1Fp {
+  static constexpr int FORM = 2;
+};
+
 struct Secp256k1Fn {
   static constexpr int N = 8;
   static constexpr int BITS = 256;

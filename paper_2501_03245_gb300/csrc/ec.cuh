@@ -211,7 +211,11 @@ constexpr int kGasResidentThreads = kGasThreads * kGasCtasPerSm;
 template <int N, int BLOCK>
 struct GasSmem {
   static constexpr int NW = BLOCK / 32;
-  uint32_t tree[5][N][BLOCK];  // subtree products per level (limb-major: no bank conflicts)
+  // subtree products per level as 16-byte vectors, thread-fastest (a warp's
+  // stores of one vector are 512 contiguous bytes); every thread touches only
+  // its own column [.][.][threadIdx.x], which is what lets a kernel reuse the
+  // area as per-thread staging outside cta_invert
+  uint4 tree[5][N / 4][BLOCK];
   uint32_t warp_tot[NW][N];
   uint32_t warp_inv[NW][N];
 };
@@ -241,7 +245,8 @@ __device__ void cta_invert(uint32_t* out, const uint32_t* in, GasSmem<F::N, BLOC
 #pragma unroll
   for (int l = 0; l < 5; ++l) {
 #pragma unroll
-    for (int i = 0; i < N; ++i) sm.tree[l][i][tid] = v[i];
+    for (int g = 0; g < N / 4; ++g)
+      sm.tree[l][g][tid] = make_uint4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
     fe_shfl_xor<F>(t, v, 1 << l);
     mont_mul<F>(v, v, t);
   }
@@ -287,7 +292,13 @@ __device__ void cta_invert(uint32_t* out, const uint32_t* in, GasSmem<F::N, BLOC
   for (int l = 4; l >= 0; --l) {
     uint32_t s[N];
 #pragma unroll
-    for (int i = 0; i < N; ++i) s[i] = sm.tree[l][i][tid];
+    for (int g = 0; g < N / 4; ++g) {
+      const uint4 q = sm.tree[l][g][tid];
+      s[4 * g] = q.x;
+      s[4 * g + 1] = q.y;
+      s[4 * g + 2] = q.z;
+      s[4 * g + 3] = q.w;
+    }
     fe_shfl_xor<F>(t, s, 1 << l);
     mont_mul<F>(v, v, t);
   }

@@ -4,7 +4,7 @@
 // 12 for the 381-bit field) held in registers, in Montgomery form a*R mod q with
 // R = 2^(32N), canonical in [0, q).  A field is a traits class F with
 //   N, qinv() = -q^-1 mod 2^32, qinv62() = q^-1 mod 2^62, FORM (0 generic,
-//   1 the P-256 prime), p(i),
+//   1 the P-256 prime, 2 the secp256k1 prime), p(i),
 //   r2(i) = R^2 mod q, one(i) = R mod q, pm2(i) = q - 2.
 //
 // mont_mul is Montgomery multiplication (Algorithm 2) with the operand-scanning
@@ -164,6 +164,31 @@ ECC_DEV void p256_reduce_row(uint32_t* c, uint32_t* d) {
   d[8] = ptx::addc(d[8], 0);
 }
 
+// Reduction row of mont_mul for q = 2^256 - 2^32 - 977 (secp256k1), the
+// special-form idea of Section 4.2 applied to this prime: u q = u 2^256 -
+// u (2^32 + 977), so the row needs one 32 x 32 -> 64 product (977 u) instead
+// of N.  -q^-1 mod 2^32 is not 1 for this prime, so u = T_0 QINV stays a
+// multiplication.  Word 0 of T + u q is exactly 0 with no carry (u makes
+// T_0 = 977 u mod 2^32), and the words above it receive
+// A = u 2^224 - (u + floor(977 u / 2^32)) in the frame of d (d[k] is word
+// k + 1): A is a non-negative 256-bit value (0 when u = 0), added with one
+// carry chain whose carry lands in d's top word.
+ECC_DEV void secp256k1_reduce_row(uint32_t* c, uint32_t* d, uint32_t qinv) {
+  const uint32_t u = c[0] * qinv;
+  const uint32_t s1 = ptx::add_cc(__umulhi(u, 977u), u);
+  const uint32_t s2 = ptx::addc(0, 0);
+  uint32_t A[8];
+  A[0] = ptx::sub_cc(0, s1);
+  A[1] = ptx::subc_cc(0, s2);
+#pragma unroll
+  for (int k = 2; k < 7; ++k) A[k] = ptx::subc_cc(0, 0);
+  A[7] = ptx::subc(u, 0);
+  d[0] = ptx::add_cc(d[0], A[0]);
+#pragma unroll
+  for (int k = 1; k < 8; ++k) d[k] = ptx::addc_cc(d[k], A[k]);
+  d[8] = ptx::addc(d[8], 0);
+}
+
 // Montgomery product r = a * b * R^-1 mod q (r may alias a or b).
 template <class F>
 ECC_DEV void mont_mul(uint32_t* r, const uint32_t* a, const uint32_t* b) {
@@ -216,6 +241,10 @@ ECC_DEV void mont_mul(uint32_t* r, const uint32_t* a, const uint32_t* b) {
     c[N] = ptx::addc(c[N], 0);
     if constexpr (F::FORM == 1) {
       p256_reduce_row(c, d);
+      continue;
+    }
+    if constexpr (F::FORM == 2) {
+      secp256k1_reduce_row(c, d, F::qinv());
       continue;
     }
     // reduction row: u = T_0 * QINV, T += u * q (even and odd chains)

@@ -45,9 +45,11 @@ CURVES = [
 # Moduli that also get a second traits class with a reduction of their own
 # (fp.cuh, mont_mul): FORM 1 is the NIST P-256 prime 2^256 - 2^224 + 2^192 +
 # 2^96 - 1, whose -q^-1 mod 2^32 is 1 and whose limbs are 0, 1 and 2^32 - 1
-# only.  The main traits classes are FORM 0 (the generic Montgomery reduction).
+# only; FORM 2 is the secp256k1 prime 2^256 - 2^32 - 977.  The main traits
+# classes are FORM 0 (the generic Montgomery reduction).
 SPECIAL = {
     0xFFFFFFFF00000001000000000000000000000000FFFFFFFFFFFFFFFFFFFFFFFF: ("P256FpSpecial", 1),
+    (1 << 256) - (1 << 32) - 977: ("Secp256k1FpSpecial", 2),
 }
 
 

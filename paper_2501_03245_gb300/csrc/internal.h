@@ -81,6 +81,11 @@ cudaError_t launch_verify(int curve, size_t n, const uint8_t* hash, const uint8_
 // [offsets[i] - offsets[0], offsets[i+1] - offsets[0]) (host offsets); out: num x 2N limbs
 int msm_window(int curve, uint64_t n);
 void msm_set_window(int curve, int log2n, int c);
+// log2 of the buckets per first-level reduction chunk for an n-point MSM, and
+// the autotuner's override for the size class log2n (0 restores the default)
+int msm_reduce_log(int curve, uint64_t n);
+void msm_set_reduce_log(int curve, int log2n, int v);
+constexpr int kMsmReduceLogMax = 10;
 cudaError_t launch_msm(int curve, uint32_t num, const uint64_t* offsets, const uint32_t* points,
                        const uint32_t* scalars, uint32_t* out, cudaStream_t st);
 cudaError_t bases_create(int curve, uint64_t n, const uint32_t* points, void** handle,

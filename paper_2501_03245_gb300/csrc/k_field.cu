@@ -180,7 +180,7 @@ int field_limbs(int curve, int field) {
 
 #define ECC_FIELD_DISPATCH(curve, field, CALL)          \
   switch ((curve) * 2 + (field)) {                      \
-    case 0: { using F = Secp256k1Fp; return CALL; }     \
+    case 0: { using F = Secp256k1FpSpecial; return CALL; } \
     case 1: { using F = Secp256k1Fn; return CALL; }     \
     case 2: { using F = P256FpSpecial; return CALL; }   \
     case 3: { using F = P256Fn; return CALL; }          \
@@ -245,8 +245,13 @@ cudaError_t launch_bench_modmul(int curve, int reduction, size_t threads, int it
                                 uint32_t* sink, cudaStream_t st) {
   const unsigned b = (unsigned)((threads + 255) / 256);
   if (reduction == 1) {
-    if (curve != 1) return cudaErrorNotSupported;
-    k_bench_modmul<P256FpSpecial><<<b, 256, 0, st>>>(iters, sink);
+    if (curve == 1) {
+      k_bench_modmul<P256FpSpecial><<<b, 256, 0, st>>>(iters, sink);
+    } else if (curve == 0) {
+      k_bench_modmul<Secp256k1FpSpecial><<<b, 256, 0, st>>>(iters, sink);
+    } else {
+      return cudaErrorNotSupported;
+    }
     return cudaGetLastError();
   }
   switch (curve) {

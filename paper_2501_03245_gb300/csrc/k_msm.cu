@@ -28,6 +28,7 @@ namespace {
 
 std::mutex g_win_mu;
 std::map<std::pair<int, int>, int> g_window_table;  // (curve, floor(log2 n)) -> c
+std::map<std::pair<int, int>, int> g_chunk_table;   // (curve, floor(log2 n)) -> red_log
 
 // Cost model: one batched addition (6 modmul) per (point, window) digit plus the
 // bucket reduction, about two and a half batched additions per bucket (the walk's
@@ -73,6 +74,22 @@ void msm_set_window(int curve, int log2n, int c) {
     g_window_table.erase({curve, log2n});
   } else {
     g_window_table[{curve, log2n}] = c;
+  }
+}
+
+int msm_reduce_log(int curve, uint64_t n) {
+  if (n < 2) n = 2;
+  std::lock_guard<std::mutex> lock(g_win_mu);
+  auto it = g_chunk_table.find({curve, ilog2(n)});
+  return it != g_chunk_table.end() ? it->second : kRedLog1Default;
+}
+
+void msm_set_reduce_log(int curve, int log2n, int v) {
+  std::lock_guard<std::mutex> lock(g_win_mu);
+  if (v <= 0) {
+    g_chunk_table.erase({curve, log2n});
+  } else {
+    g_chunk_table[{curve, log2n}] = v;
   }
 }
 

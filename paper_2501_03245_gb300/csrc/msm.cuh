@@ -41,7 +41,8 @@ struct MsmInst {
   // buckets, one per window.
   uint64_t pre_stride;
   uint32_t Wr;           // bucket rows (windows reduced separately)
-  uint32_t pad;
+  uint32_t red_log;      // log2 of the buckets per first-level reduction chunk
+  uint64_t digit_off;    // first rank slot: digit w of point j at digit_off + w n + j
 };
 
 // ------------------------------------------------------------------ digits
@@ -101,9 +102,14 @@ ECC_DEV int find_inst(const MsmInst* inst, int num, uint64_t g) {
   return lo;
 }
 
+// Histogram of the bucket ids.  The count a digit's atomic increment returns is
+// its rank inside its bucket; the rank is kept (digit w of point j of an
+// instance at digit_off + w n + j, so a warp's writes of one window are
+// contiguous) and the scatter places the digit at off[b] + rank with no atomics
+// of its own.
 template <class C>
 __global__ void k_msm_count(const MsmInst* inst, int num, const uint32_t* __restrict__ scalars,
-                            uint64_t total, uint32_t* __restrict__ count) {
+                            uint64_t total, uint32_t* __restrict__ count, uint32_t* __restrict__ rank) {
   const uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (g >= total) return;
   const MsmInst in = inst[find_inst(inst, num, g)];
@@ -113,9 +119,10 @@ __global__ void k_msm_count(const MsmInst* inst, int num, const uint32_t* __rest
   scalar_mod_r<C>(k);
   const uint32_t half = 1u << (in.c - 1);
   const uint32_t row = in.pre_stride ? 0u : half;
+  const uint64_t slot = in.digit_off + (g - in.scalar_off);
   for_each_digit(k, in.c, in.W, [&](int w, int d) {
     const uint32_t b = in.bucket_base + w * row + (uint32_t)(d < 0 ? -d : d) - 1;
-    atomicAdd(count + b, 1u);
+    rank[slot + (uint64_t)w * in.n] = atomicAdd(count + b, 1u);
   });
 }
 
@@ -125,9 +132,9 @@ __global__ void k_msm_count(const MsmInst* inst, int num, const uint32_t* __rest
 // per-chunk bucket cursor starts there).
 template <class C>
 __global__ void k_msm_scatter(const MsmInst* inst, int num, const uint32_t* __restrict__ scalars,
-                              uint64_t total, uint32_t* __restrict__ cursor,
-                              uint32_t* __restrict__ vals, uint64_t n_chunks,
-                              uint32_t* __restrict__ cur) {
+                              uint64_t total, const uint32_t* __restrict__ off,
+                              const uint32_t* __restrict__ rank, uint32_t* __restrict__ vals,
+                              uint64_t n_chunks, uint32_t* __restrict__ cur) {
   const uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (g >= total) return;
   const MsmInst in = inst[find_inst(inst, num, g)];
@@ -138,9 +145,10 @@ __global__ void k_msm_scatter(const MsmInst* inst, int num, const uint32_t* __re
   const uint32_t half = 1u << (in.c - 1);
   const uint32_t row = in.pre_stride ? 0u : half;
   const uint64_t pidx = in.point_off + (g - in.scalar_off);
+  const uint64_t slot = in.digit_off + (g - in.scalar_off);
   for_each_digit(k, in.c, in.W, [&](int w, int d) {
     const uint32_t b = in.bucket_base + w * row + (uint32_t)(d < 0 ? -d : d) - 1;
-    const uint32_t p = atomicAdd(cursor + b, 1u);
+    const uint32_t p = off[b] + rank[slot + (uint64_t)w * in.n];
     const uint32_t idx = (uint32_t)(pidx + (uint64_t)w * in.pre_stride);  // < 2^31 (host check)
     vals[(uint64_t)(p % kAccChunk) * n_chunks + p / kAccChunk] = idx | (d < 0 ? 0x80000000u : 0u);
     if (p % kAccChunk == 0) cur[p / kAccChunk] = b;
@@ -171,7 +179,6 @@ struct AccArgs {
   PtSoA<F> S;             // running sum per chunk
   PtSoA<F> partial;       // partial bucket sums
   SoA<F> M;               // GAS prefix products
-  SoA<F> D;               // this round's denominators
   uint64_t per_cta;
 };
 
@@ -251,31 +258,41 @@ ECC_DEV AccCls acc_classify(const AccArgs<C>& a, uint64_t c, int j, uint32_t ent
   return k;
 }
 
-// ---- 8-limb fields: one round with every operand staged in shared memory.
+// ---- One round with every operand staged in shared memory (cp.async).
 // Entry j of every chunk is added to the chunk's running sum S (or starts a
-// new one at a bucket boundary).  Each thread owns kStageVecs 16-byte vectors of
-// shared memory (layout [vector][thread], so a warp's copies of one vector are
-// 512 contiguous bytes) after the GAS scratch.  While a thread computes on its
-// item k, the cp.async copies of item k+1's operands and the first-level loads
-// of item k+2 (its sorted entry and its chunk's bucket cursor) are in flight,
-// and so is item k+1's bucket end off[pb + 1]: the gathers behind the sorted
-// entries never stall the arithmetic.  Compress stages only x of S and of the
-// base (the compress step of Section 3.3); y is read, directly, only when an
-// operand may be O (x = 0) or the two x agree (doubling or P = -T), which
-// random inputs almost never hit.  DCWPA stages S, the base and the prefix
-// product, and keeps the operands in registers through the finish, so no
-// denominator array exists.
-constexpr int kStageVecs = 10;  // S.x 0-1, S.y 2-3, base.x 4-5, base.y 6-7, prefix 8-9
-
-template <int BLOCK>
+// new one at a bucket boundary).  Each thread owns 5 G 16-byte vectors of
+// shared memory (G = N / 4 vectors per field element; layout [vector][thread],
+// so a warp's copies of one vector are 512 contiguous bytes).  They are the
+// thread's own column of the GAS tree, which is dead outside cta_invert: the
+// staging costs no shared memory of its own.  While a thread computes on its
+// item k, the copies of item k+1's operands and the first-level loads of item
+// k+2 (its sorted entry and its chunk's bucket cursor, into registers) are in
+// flight, and so is item k+1's bucket end off[pb + 1], so the gathers behind
+// the sorted entries do not stall the arithmetic.  Compress stages only x of S
+// and of the base (the compress step of Section 3.3); y is read, directly, only
+// when an operand may be O (x = 0) or the two x agree (doubling or P = -T),
+// which random inputs almost never hit.  DCWPA stages S, the base and the prefix
+// product.  With 8 limbs it holds all of them in registers from the top of the
+// item, so the next item's copies start at once; with 12 limbs (no registers to
+// spare) it computes the item's two DCWPA products from the staged values first,
+// then loads the finish operands and only then starts the next item's copies.
+// No denominator array exists for either width.
+template <int N, int BLOCK>
 struct Stage {
-  uint4* v;  // [kStageVecs][BLOCK]
+  static constexpr int G = N / 4;
+  // vector bases: S.x, S.y, base.x, base.y, prefix product
+  static constexpr int SX = 0, SY = G, BX = 2 * G, BY = 3 * G, PRE = 4 * G;
+  uint4* v;  // [5 G][BLOCK]
   ECC_DEV uint4* at(int k) const { return v + k * BLOCK + threadIdx.x; }
-  // vectors k0, k0 + 1 -> 8 words
   ECC_DEV void get(int k0, uint32_t* r) const {
-    const uint4 p = *at(k0), q = *at(k0 + 1);
-    r[0] = p.x; r[1] = p.y; r[2] = p.z; r[3] = p.w;
-    r[4] = q.x; r[5] = q.y; r[6] = q.z; r[7] = q.w;
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const uint4 p = *at(k0 + g);
+      r[4 * g] = p.x;
+      r[4 * g + 1] = p.y;
+      r[4 * g + 2] = p.z;
+      r[4 * g + 3] = p.w;
+    }
   }
 };
 
@@ -283,25 +300,25 @@ struct Stage {
 // and with `full` also y of both and the prefix product.  The base is touched
 // only for an existing entry (v is meaningful only then).
 template <class C, int BLOCK>
-ECC_DEV void acc_stage(const Stage<BLOCK>& sg, const AccArgs<C>& a, uint64_t c, uint32_t v, bool live,
-                       bool full) {
-  const SoA<typename C::Fp>& sx = a.S.x;
-  ptx::cp_async16(sg.at(0), sx.vec + c);
-  ptx::cp_async16(sg.at(1), sx.vec + sx.stride + c);
+ECC_DEV void acc_stage(const Stage<C::Fp::N, BLOCK>& sg, const AccArgs<C>& a, uint64_t c, uint32_t v,
+                       bool live, bool full) {
+  using S = Stage<C::Fp::N, BLOCK>;
+#pragma unroll
+  for (int g = 0; g < S::G; ++g) ptx::cp_async16(sg.at(S::SX + g), a.S.x.vec + g * a.S.x.stride + c);
   if (full) {
-    const SoA<typename C::Fp>& sy = a.S.y;
-    ptx::cp_async16(sg.at(2), sy.vec + c);
-    ptx::cp_async16(sg.at(3), sy.vec + sy.stride + c);
-    ptx::cp_async16(sg.at(8), a.M.vec + c);
-    ptx::cp_async16(sg.at(9), a.M.vec + a.M.stride + c);
+#pragma unroll
+    for (int g = 0; g < S::G; ++g) {
+      ptx::cp_async16(sg.at(S::SY + g), a.S.y.vec + g * a.S.y.stride + c);
+      ptx::cp_async16(sg.at(S::PRE + g), a.M.vec + g * a.M.stride + c);
+    }
   }
   if (live) {
     const uint4* p = base_ptr(a, v);
-    ptx::cp_async16(sg.at(4), p);
-    ptx::cp_async16(sg.at(5), p + 1);
+#pragma unroll
+    for (int g = 0; g < S::G; ++g) ptx::cp_async16(sg.at(S::BX + g), p + g);
     if (full) {
-      ptx::cp_async16(sg.at(6), p + 2);
-      ptx::cp_async16(sg.at(7), p + 3);
+#pragma unroll
+      for (int g = 0; g < S::G; ++g) ptx::cp_async16(sg.at(S::BY + g), p + S::G + g);
     }
   }
   ptx::cp_async_commit();
@@ -309,10 +326,13 @@ ECC_DEV void acc_stage(const Stage<BLOCK>& sg, const AccArgs<C>& a, uint64_t c, 
 
 template <class C, int BLOCK>
 __device__ void acc_round_staged(const AccArgs<C>& a, int j, uint32_t entries, uint64_t begin,
-                                 uint64_t end, const Stage<BLOCK>& sg, GasSmem<8, BLOCK>& sm) {
+                                 uint64_t end, GasSmem<C::Fp::N, BLOCK>& sm) {
   using F = typename C::Fp;
-  constexpr int N = 8;
-  static_assert(F::N == N, "8-limb fields only");
+  constexpr int N = F::N;
+  using S = Stage<N, BLOCK>;
+  constexpr bool kEarly = N <= 8;
+  static_assert(sizeof(sm.tree) >= 5 * S::G * BLOCK * sizeof(uint4), "staging fits the GAS tree");
+  const S sg{&sm.tree[0][0][0]};
   const uint64_t i0 = begin + threadIdx.x;
   const uint64_t row = (uint64_t)j * a.n_chunks;
   auto is_live = [&](uint64_t c) { return (uint32_t)(c * kAccChunk + j) < entries; };
@@ -334,8 +354,8 @@ __device__ void acc_round_staged(const AccArgs<C>& a, int j, uint32_t entries, u
   for (uint64_t c = i0; c < end; c += BLOCK) {
     ptx::cp_async_wait_all();
     uint32_t x1[N], x2[N];
-    sg.get(0, x1);
-    sg.get(4, x2);
+    sg.get(S::SX, x1);
+    sg.get(S::BX, x2);
     const uint64_t cn = c + BLOCK;
     uint32_t o1 = 0, v2 = 0, pb2 = 0;
     if (cn < end) {
@@ -363,7 +383,8 @@ __device__ void acc_round_staged(const AccArgs<C>& a, int j, uint32_t entries, u
     v0 = v1; pb0 = pb1; o0 = o1;
     v1 = v2; pb1 = pb2;
   }
-  // ---- inverse of the CTA's product (GAS, Section 3.2)
+  // ---- inverse of the CTA's product (GAS, Section 3.2); the staging area is
+  // the tree inside, so every copy of this thread has landed (waited above)
   uint32_t inv[N];
   cta_invert<F, BLOCK>(inv, run, sm);
   if (i0 >= end) return;
@@ -379,15 +400,11 @@ __device__ void acc_round_staged(const AccArgs<C>& a, int j, uint32_t entries, u
   }
   for (uint64_t c = last;; c -= BLOCK) {
     ptx::cp_async_wait_all();
-    uint32_t xs[N], ys[N], xp[N], yp[N], pre[N];
-    sg.get(0, xs);
-    sg.get(2, ys);
-    sg.get(4, xp);
-    sg.get(6, yp);
-    sg.get(8, pre);
     const bool more = c >= i0 + BLOCK;
     uint32_t o1 = 0, v2 = 0, pb2 = 0;
-    if (more) {
+    // next item's copies and bucket end, first-level loads of the one after
+    auto ahead = [&]() {
+      if (!more) return;
       const uint64_t cn = c - BLOCK;
       acc_stage<C, BLOCK>(sg, a, cn, v1, is_live(cn), true);
       if (j > 0) o1 = a.off[pb1 + 1];
@@ -395,19 +412,56 @@ __device__ void acc_round_staged(const AccArgs<C>& a, int j, uint32_t entries, u
         v2 = a.vals[row + cn - BLOCK];
         pb2 = a.cur[cn - BLOCK];
       }
-    }
+    };
     const AccCls k = acc_classify(a, c, j, entries, pb0, o0);
-    if (v0 & 0x80000000u) fe_neg<F>(yp, yp);
-    uint32_t d[N];
+    const bool neg = (v0 & 0x80000000u) != 0;
+    uint32_t xs[N], ys[N], xp[N], yp[N], d[N], mine[N];
     int kind = ADD_RET_T;
-    if (!k.live || k.start) {
-      fe_set_one<F>(d);
+    if constexpr (kEarly) {
+      uint32_t pre[N];
+      sg.get(S::SX, xs);
+      sg.get(S::SY, ys);
+      sg.get(S::BX, xp);
+      sg.get(S::BY, yp);
+      sg.get(S::PRE, pre);
+      ahead();
+      if (neg) fe_neg<F>(yp, yp);
+      if (!k.live || k.start) {
+        fe_set_one<F>(d);
+      } else {
+        kind = add_den<C>(d, xs, ys, xp, yp);
+      }
+      mont_mul<F>(mine, inv, pre);
+      mont_mul<F>(inv, inv, d);
     } else {
-      kind = add_den<C>(d, xs, ys, xp, yp);
+      if (!k.live || k.start) {
+        fe_set_one<F>(d);
+      } else {
+        sg.get(S::SX, xs);
+        sg.get(S::BX, xp);
+        if (fe_is_zero<F>(xs) || fe_is_zero<F>(xp) || fe_eq<F>(xs, xp)) {
+          sg.get(S::SY, ys);
+          sg.get(S::BY, yp);
+          if (neg) fe_neg<F>(yp, yp);
+          kind = add_den<C>(d, xs, ys, xp, yp);
+        } else {
+          kind = ADD_REGULAR;
+          fe_sub<F>(d, xp, xs);
+        }
+      }
+      {
+        uint32_t pre[N];
+        sg.get(S::PRE, pre);
+        mont_mul<F>(mine, inv, pre);
+      }
+      mont_mul<F>(inv, inv, d);
+      sg.get(S::SX, xs);
+      sg.get(S::SY, ys);
+      sg.get(S::BX, xp);
+      sg.get(S::BY, yp);
+      ahead();
+      if (neg) fe_neg<F>(yp, yp);
     }
-    uint32_t mine[N];
-    mont_mul<F>(mine, inv, pre);
-    mont_mul<F>(inv, inv, d);
     if (k.live) {
       if (k.start) {
         if (j > 0) {
@@ -426,95 +480,6 @@ __device__ void acc_round_staged(const AccArgs<C>& a, int j, uint32_t entries, u
   }
 }
 
-// ---- 12-limb fields: the round as a batch_round client.  Compress loads only
-// x of S and of the base (y only when an operand may be O or the x agree) and
-// stores the round's denominator (holding the DCWPA operands in registers
-// would spill at 12 limbs); DCWPA reloads the denominator, finish the operands.
-// Compress issues the first-level loads of the thread's next item (its sorted
-// entry and its chunk's bucket cursor) one item ahead.
-template <class C, int BLOCK>
-struct AccRound {
-  using F = typename C::Fp;
-  static constexpr int N = F::N;
-  static constexpr int OPS = 1;
-  const AccArgs<C>* a;
-  int j;
-  uint32_t entries;
-  uint64_t begin, end;  // this CTA's chunks
-  uint64_t nc = ~0ull;  // chunk whose loads below were issued ahead
-  uint32_t nv, ncur;
-  ECC_DEV void fetch(uint64_t c, uint32_t& v, uint32_t& pb) const {
-    v = a->vals[(uint64_t)j * a->n_chunks + c];
-    pb = a->cur[c];
-  }
-  ECC_DEV AccCls classify(uint64_t c, uint32_t pb) const {
-    const bool need = j > 0 && (uint32_t)(c * kAccChunk + j) < entries;
-    return acc_classify(*a, c, j, entries, pb, need ? a->off[pb + 1] : 0u);
-  }
-  ECC_DEV void den_c(size_t c, int, uint32_t* d) {
-    uint32_t v, pb;
-    if (nc == c) {
-      v = nv;
-      pb = ncur;
-    } else {
-      fetch(c, v, pb);
-    }
-    if (c + BLOCK < end) {
-      nc = c + BLOCK;
-      fetch(nc, nv, ncur);
-    }
-    const AccCls k = classify(c, pb);
-    if (!k.live || k.start) {
-      fe_set_one<F>(d);
-    } else {
-      uint32_t x1[N], x2[N];
-      a->S.x.load(c, x1);
-      load_base_x<C>(*a, v, x2);
-      if (fe_is_zero<F>(x1) || fe_is_zero<F>(x2) || fe_eq<F>(x1, x2)) {
-        uint32_t y1[N], y2[N];
-        a->S.y.load(c, y1);
-        load_base_y<C>(*a, v, y2);
-        add_den<C>(d, x1, y1, x2, y2);
-      } else {
-        fe_sub<F>(d, x2, x1);
-      }
-    }
-    a->D.store(c, d);
-  }
-  ECC_DEV void den_d(size_t c, int, uint32_t* d) { a->D.load(c, d); }
-  ECC_DEV void finish(size_t c, const uint32_t (*inv)[N]) {
-    uint32_t v, pb;
-    fetch(c, v, pb);
-    const AccCls k = classify(c, pb);
-    if (!k.live) return;
-    uint32_t x1[N], y1[N], x2[N], y2[N];
-    load_base<C>(*a, v, x2, y2);
-    if (k.start) {
-      if (j > 0) {
-        a->S.load(c, x1, y1);
-        a->partial.store(partial_slot(*a, k.prev, c), x1, y1);
-        a->cur[c] = k.bucket;
-      }
-      a->S.store(c, x2, y2);
-    } else {
-      a->S.load(c, x1, y1);
-      const int kind = add_kind<C>(x1, y1, x2, y2);
-      add_finish<C>(x1, y1, kind, inv[0], x1, y1, x2, y2);
-      a->S.store(c, x1, y1);
-    }
-  }
-};
-
-// Fields whose accumulation stages its operands in shared memory.
-template <class F>
-inline constexpr bool kAccStaged = F::N == 8;
-
-// Dynamic shared memory of k_msm_accumulate.
-template <int N, int BLOCK>
-__host__ __device__ constexpr size_t acc_smem_bytes() {
-  return sizeof(GasSmem<N, BLOCK>) + (N == 8 ? (size_t)kStageVecs * BLOCK * 16 : 0);
-}
-
 template <class C, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, kGasResidentThreads / BLOCK) k_msm_accumulate(AccArgs<C> a) {
   using F = typename C::Fp;
@@ -526,17 +491,7 @@ __global__ void __launch_bounds__(BLOCK, kGasResidentThreads / BLOCK) k_msm_accu
   uint64_t end = begin + a.per_cta;
   if (end > used) end = used;
   if (end < begin) end = begin;
-  if constexpr (kAccStaged<F>) {
-    static_assert(sizeof(GasSmem<N, BLOCK>) % 16 == 0, "staging area alignment");
-    const Stage<BLOCK> sg{reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(&sm) +
-                                                   sizeof(GasSmem<N, BLOCK>))};
-    for (int j = 0; j < kAccChunk; ++j) acc_round_staged<C, BLOCK>(a, j, entries, begin, end, sg, sm);
-  } else {
-    for (int j = 0; j < kAccChunk; ++j) {
-      AccRound<C, BLOCK> rd{&a, j, entries, begin, end};
-      batch_round<F, BLOCK>(rd, begin, end, a.M, sm);
-    }
-  }
+  for (int j = 0; j < kAccChunk; ++j) acc_round_staged<C, BLOCK>(a, j, entries, begin, end, sm);
   // flush the last running sum of every chunk
   for (uint64_t c = begin + threadIdx.x; c < end; c += BLOCK) {
     uint32_t xs[N], ys[N];
@@ -548,10 +503,10 @@ __global__ void __launch_bounds__(BLOCK, kGasResidentThreads / BLOCK) k_msm_accu
 // ------------------------------------------------------------------ reduction
 //
 // Window sum sum_b b E_b (E_b the bucket sums, b = 1 .. 2^(c-1)) in levels.
-// Level 1 cuts each window row into chunks of kRedChunk1 consecutive buckets;
+// Level 1 cuts each window row into chunks of K = 2^red_log consecutive buckets;
 // chunk u (buckets lo .. hi-1, 0-based) yields the plain sum R_u and the sum
 // S_u = sum_e (e - lo + 1) E_e weighted from the chunk's own first bucket, so
-// the window sum is sum_u (S_u + u (kRedChunk1 R_u)).  Every later level takes
+// the window sum is sum_u (S_u + u (K R_u)).  Every later level takes
 // elements (R~_e, S~_e) whose target is sum_e (S~_e + e R~_e) and cuts them
 // into chunks of kRedChunkN: chunk v yields R_v = sum R~_e and
 // S_v = sum_e (S~_e + (e - lo) R~_e), and hands (kRedChunkN R_v, S_v) on, until
@@ -561,8 +516,9 @@ __global__ void __launch_bounds__(BLOCK, kGasResidentThreads / BLOCK) k_msm_accu
 // Before level 1 the partial sums of every bucket are folded into one (a
 // batched affine pairwise tree, ceil(log2 k) rounds for k partials; CTAs take
 // equal shares of the partial slots, so a bucket holding many entries costs
-// rounds only in the CTA that owns it).  Level 1 then has 2^(c-1) / kRedChunk1
-// independent chunks per window row and runs as batched affine additions
+// rounds only in the CTA that owns it).  Level 1 then has 2^(c-1) / K
+// independent chunks per window row (2^red_log buckets each, a per-instance
+// layout parameter the autotuner picks) and runs as batched affine additions
 // (Section 3.3) with one inversion per CTA per round (Section 3.2): the running
 // sums R and S of every chunk walk the chunk's buckets downwards, adding the
 // bucket sum to R ("A" event) and then R to S ("S" event).  An S event uses
@@ -570,8 +526,8 @@ __global__ void __launch_bounds__(BLOCK, kGasResidentThreads / BLOCK) k_msm_accu
 // chunk of k buckets takes k + 1 rounds.  The short upper levels run in
 // Jacobian coordinates, one thread per chunk.
 
-constexpr uint32_t kRedChunk1 = 32;      // buckets per first-level chunk
-constexpr int kRedLog1 = 5;
+constexpr int kRedLog1Default = 5;      // log2 buckets per first-level chunk, by default
+constexpr int kRedLog1Max = 10;
 constexpr uint32_t kRedChunkN = 4;       // elements per chunk on the later levels
 constexpr int kRedLogN = 2;
 
@@ -740,7 +696,8 @@ struct AffRedArgs {
   uint32_t* cur_e;        // 1 + the bucket the next event belongs to
   uint32_t* cur_a;        // whether that bucket's A event is done
   uint32_t* lo_b;         // first bucket of the item
-  Jac<F>* out_R;          // kRedChunk1 R per item (Jacobian, Z = 1 or O)
+  uint32_t* rlog;         // log2 of the item's chunk size (its instance's red_log)
+  Jac<F>* out_R;          // 2^rlog R per item (Jacobian, Z = 1 or O)
   Jac<F>* out_S;
   uint64_t per_cta;
 };
@@ -843,21 +800,28 @@ struct AffRedRound {
   }
 };
 
-// R <- 2 R for every item (batched PDBL)
+// R <- 2 R for every item whose chunk needs more than k doublings (batched PDBL)
 template <class C>
 struct AffDblRound {
   using F = typename C::Fp;
   static constexpr int N = F::N;
   static constexpr int OPS = 1;
   const AffRedArgs<C>* a;
-  bool live;
+  uint32_t k;
+  bool live, skip;
   ECC_DEV void den_c(size_t i, int, uint32_t* d) {
+    skip = a->rlog[i] <= k;
+    if (skip) {
+      fe_set_one<F>(d);
+      return;
+    }
     uint32_t x[N], y[N];
     a->R.load(i, x, y);
     live = dbl_den<C>(d, y);
   }
   ECC_DEV void den_d(size_t i, int j, uint32_t* d) { den_c(i, j, d); }
   ECC_DEV void finish(size_t i, const uint32_t (*inv)[N]) {
+    if (skip) return;
     uint32_t x[N], y[N];
     a->R.load(i, x, y);
     dbl_finish<C>(x, y, live, inv[0], x, y);
@@ -883,9 +847,11 @@ __global__ void __launch_bounds__(BLOCK, kGasResidentThreads / BLOCK)
     const uint32_t B = 1u << (in.c - 1);
     const uint64_t local = t - rg.t0;
     const uint32_t w = (uint32_t)(local / rg.chunks), u = (uint32_t)(local % rg.chunks);
-    const uint32_t lo = in.bucket_base + w * B + u * kRedChunk1;
-    const uint32_t hi = lo + (B - u * kRedChunk1 < kRedChunk1 ? B - u * kRedChunk1 : kRedChunk1);
+    const uint32_t K = 1u << in.red_log;
+    const uint32_t lo = in.bucket_base + w * B + u * K;
+    const uint32_t hi = lo + (B - u * K < K ? B - u * K : K);
     a.lo_b[t] = lo;
+    a.rlog[t] = in.red_log;
     a.cur_e[t] = hi;
     a.cur_a[t] = 0;
     uint32_t z[N];
@@ -895,15 +861,19 @@ __global__ void __launch_bounds__(BLOCK, kGasResidentThreads / BLOCK)
     more = true;
   }
   // one bounded loop: each round completes at least one event of every live
-  // item, and an item has at most 2 kRedChunk1 events
+  // item, and an item has at most 2^(rlog + 1) events
   while (__syncthreads_or(more)) {
     AffRedRound<C> rd{&a};
     rd.more = false;
     batch_round<F, BLOCK>(rd, begin, end, a.M, sm);
     more = rd.more;
   }
-  for (int k = 0; k < kRedLog1; ++k) {
-    AffDblRound<C> rd{&a};
+  // R <- 2^rlog R: as many doubling rounds as the CTA's largest chunk needs
+  for (uint32_t k = 0; k < (uint32_t)kRedLog1Max; ++k) {
+    bool want = false;
+    for (uint64_t t = begin + threadIdx.x; t < end; t += BLOCK) want |= a.rlog[t] > k;
+    if (!__syncthreads_or(want)) break;
+    AffDblRound<C> rd{&a, k};
     batch_round<F, BLOCK>(rd, begin, end, a.M, sm);
   }
   for (uint64_t t = begin + threadIdx.x; t < end; t += BLOCK) {

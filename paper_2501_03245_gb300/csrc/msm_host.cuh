@@ -6,6 +6,7 @@
 #pragma once
 #include <algorithm>
 #include <map>
+#include <tuple>
 #include <vector>
 
 #include "internal.h"
@@ -18,6 +19,7 @@ namespace ecc {
 namespace msm_detail {
 
 constexpr int kAccBlock = kGasThreads;
+static_assert(kRedLog1Max == kMsmReduceLogMax, "one bound for the first-level reduction chunk");
 
 inline int scalar_bits(int curve) {
   switch (curve) {
@@ -49,13 +51,13 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
   const uint64_t sz_inst = up(num * sizeof(MsmInst));
   const uint64_t sz_b1 = up((B + 1) * 4);
   const uint64_t sz_kv = up(kAccChunk * NC * 4), sz_cur = up(NC * 4);
+  const uint64_t sz_rank = up(std::max<uint64_t>(L.entries_max, 1) * 4);
   const uint64_t sz_S = soa_bytes<F>(NC), sz_P = soa_bytes<F>(n_part);
   const uint64_t sz_ops = up(n_part * 4);
-  // per chunk: running sum (x, y), prefix product and, where the accumulation
-  // does not keep its operands in registers, the round's denominator
-  constexpr bool kHold = kAccStaged<F>;
-  constexpr uint64_t kChunkArrays = kHold ? 3 : 4;
-  const uint64_t bytes = sz_inst + 5 * sz_b1 + sz_kv + sz_cur + kChunkArrays * sz_S + 3 * sz_P + sz_ops + 256;
+  // per chunk: running sum (x, y) and prefix product
+  constexpr uint64_t kChunkArrays = 3;
+  const uint64_t bytes =
+      sz_inst + 4 * sz_b1 + sz_kv + sz_cur + sz_rank + kChunkArrays * sz_S + 3 * sz_P + sz_ops + 256;
   Scratch ws;
   cudaError_t e = ws.alloc(bytes, st);
   if (e != cudaSuccess) return e;
@@ -64,7 +66,7 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
   MsmInst* d_inst = reinterpret_cast<MsmInst*>(take(sz_inst));
   uint32_t* count = reinterpret_cast<uint32_t*>(take(sz_b1));
   uint32_t* off = reinterpret_cast<uint32_t*>(take(sz_b1));
-  uint32_t* cursor = reinterpret_cast<uint32_t*>(take(sz_b1));
+  uint32_t* rank = reinterpret_cast<uint32_t*>(take(sz_rank));
   uint32_t* npart = reinterpret_cast<uint32_t*>(take(sz_b1));
   uint32_t* poff = reinterpret_cast<uint32_t*>(take(sz_b1));
   uint32_t* vals = reinterpret_cast<uint32_t*>(take(sz_kv));
@@ -78,16 +80,15 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
   e = cudaMemsetAsync(count, 0, (B + 1) * 4, st);
   if (e != cudaSuccess) return e;
   const unsigned pb = (unsigned)((L.total_points + 255) / 256);
-  if (L.total_points) k_msm_count<C><<<pb, 256, 0, st>>>(d_inst, num, scalars, L.total_points, count);
+  if (L.total_points)
+    k_msm_count<C><<<pb, 256, 0, st>>>(d_inst, num, scalars, L.total_points, count, rank);
   e = exclusive_scan(count, B, off, st);
-  if (e != cudaSuccess) return e;
-  e = cudaMemcpyAsync(cursor, off, B * 4, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return e;
   if (B) k_msm_npart<<<(unsigned)((B + 255) / 256), 256, 0, st>>>(off, (uint32_t)B, npart);
   e = exclusive_scan(npart, B, poff, st);
   if (e != cudaSuccess) return e;
   if (L.total_points)
-    k_msm_scatter<C><<<pb, 256, 0, st>>>(d_inst, num, scalars, L.total_points, cursor, vals, NC,
+    k_msm_scatter<C><<<pb, 256, 0, st>>>(d_inst, num, scalars, L.total_points, off, rank, vals, NC,
                                           cur);
   // ---- 3: bucket accumulation (batched affine, one launch)
   AccArgs<C> a;
@@ -100,7 +101,6 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
   a.bases = bases_mont;
   a.S = PtSoA<F>{SoA<F>{sbuf, NC}, SoA<F>{sbuf + sz_S / 16, NC}};
   a.M = SoA<F>{sbuf + 2 * sz_S / 16, NC};
-  a.D = kHold ? SoA<F>{nullptr, NC} : SoA<F>{sbuf + 3 * sz_S / 16, NC};
   a.partial = PtSoA<F>{SoA<F>{pbuf, n_part}, SoA<F>{pbuf + sz_P / 16, n_part}};
   uint64_t ctas = (uint64_t)device_sm_count() * kGasCtasPerSm;
   uint64_t per = (NC + ctas - 1) / ctas;
@@ -108,11 +108,10 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
   ctas = (NC + per - 1) / per;
   a.per_cta = per;
   const size_t smem = sizeof(GasSmem<N, kAccBlock>);
-  const size_t acc_smem = acc_smem_bytes<N, kAccBlock>();
   e = cudaFuncSetAttribute(k_msm_accumulate<C, kAccBlock>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)acc_smem);
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_msm_accumulate<C, kAccBlock><<<(unsigned)ctas, kAccBlock, acc_smem, st>>>(a);
+  k_msm_accumulate<C, kAccBlock><<<(unsigned)ctas, kAccBlock, smem, st>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // ---- fold the partial sums of every bucket into its first slot
@@ -133,17 +132,19 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
   // ---- 4: bucket reduction.  Instances are grouped by window width (same
   // level structure); the items of every level are laid out group-major so a
   // level of all groups is one launch.
-  // groups by (window width, bucket rows per instance)
-  std::map<std::pair<uint32_t, uint32_t>, std::vector<uint32_t>> groups;
-  for (int i = 0; i < num; ++i) groups[{L.inst[i].c, L.inst[i].Wr}].push_back((uint32_t)i);
+  // groups by (window width, bucket rows per instance, first-level chunk)
+  std::map<std::tuple<uint32_t, uint32_t, uint32_t>, std::vector<uint32_t>> groups;
+  for (int i = 0; i < num; ++i)
+    groups[{L.inst[i].c, L.inst[i].Wr, L.inst[i].red_log}].push_back((uint32_t)i);
   std::vector<std::vector<uint32_t>> elems;  // per group: elements per row, by level
   std::vector<uint64_t> rows;
   for (auto& g : groups) {
-    std::vector<uint32_t> el{1u << (g.first.first - 1)};
-    el.push_back((el[0] + kRedChunk1 - 1) / kRedChunk1);
+    std::vector<uint32_t> el{1u << (std::get<0>(g.first) - 1)};
+    const uint32_t K = 1u << std::get<2>(g.first);
+    el.push_back((el[0] + K - 1) / K);
     while (el.back() > 1) el.push_back((el.back() + kRedChunkN - 1) / kRedChunkN);
     elems.push_back(el);
-    rows.push_back((uint64_t)g.second.size() * g.first.second);
+    rows.push_back((uint64_t)g.second.size() * std::get<1>(g.first));
   }
   const size_t n_groups = elems.size();
   size_t levels = 0;
@@ -187,7 +188,7 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
   uint64_t seg_words = 0;
   for (size_t l = 2; l <= levels; ++l) seg_words += up(segs[l].size() * sizeof(LevelSeg));
   const uint64_t sz_red = up(ranges.size() * sizeof(RedRange)) + up(num * 8ull) + seg_words +
-                          2 * up(jac_total * sizeof(Jac<F>)) + 3 * up(items * 4) +
+                          2 * up(jac_total * sizeof(Jac<F>)) + 4 * up(items * 4) +
                           5 * soa_bytes<F>(std::max<uint64_t>(items, 1)) + 256;
   Scratch rs;
   e = rs.alloc(sz_red, st);
@@ -203,6 +204,7 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
   uint32_t* cur_e = reinterpret_cast<uint32_t*>(take_r(items * 4));
   uint32_t* cur_a = reinterpret_cast<uint32_t*>(take_r(items * 4));
   uint32_t* lo_b = reinterpret_cast<uint32_t*>(take_r(items * 4));
+  uint32_t* rlog = reinterpret_cast<uint32_t*>(take_r(items * 4));
   const uint64_t IT = std::max<uint64_t>(items, 1);
   uint4* rbuf = reinterpret_cast<uint4*>(take_r(5 * soa_bytes<F>(IT)));
   e = upload_words(d_ranges, ranges.data(), ranges.size() * sizeof(RedRange), st);
@@ -228,6 +230,7 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
     r.cur_e = cur_e;
     r.cur_a = cur_a;
     r.lo_b = lo_b;
+    r.rlog = rlog;
     r.out_R = JR;
     r.out_S = JS;
     uint64_t rctas = (uint64_t)device_sm_count() * kGasCtasPerSm;
@@ -274,7 +277,8 @@ inline Layout plan(int curve, uint32_t num, const uint64_t* sizes, const uint64_
     m.scalar_off = scalar_off[i];
     m.pre_stride = pre_c > 0 ? pre_stride : 0;
     m.Wr = pre_c > 0 ? 1u : m.W;
-    m.pad = 0;
+    m.red_log = (uint32_t)std::min<int>(msm_reduce_log(curve, sizes[i]), (int)m.c - 1);
+    m.digit_off = L.entries_max;
     L.buckets += (uint64_t)m.Wr << (m.c - 1);
     L.entries_max += (uint64_t)m.W * m.n;
     L.total_points += m.n;

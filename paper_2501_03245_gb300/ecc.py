@@ -55,6 +55,8 @@ _SIGS = {
     "ecc_bases_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "ecc_msm_window": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t]),
     "ecc_msm_set_window": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "ecc_msm_reduce_chunk": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t]),
+    "ecc_msm_set_reduce_chunk": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "ecc_bench_imad": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "ecc_bench_inv": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_size_t, ctypes.c_int,
                                      ctypes.c_void_p, ctypes.c_void_p]),
@@ -254,6 +256,17 @@ def ecc_msm_window(curve, n):
 
 def ecc_msm_set_window(curve, log2_n, c):
     return _check(load().ecc_msm_set_window(curve, log2_n, c))
+
+
+def ecc_msm_reduce_chunk(curve, n):
+    rc = load().ecc_msm_reduce_chunk(curve, n)
+    if rc < 0:
+        _check(rc)
+    return rc
+
+
+def ecc_msm_set_reduce_chunk(curve, log2_n, log2_chunk):
+    return _check(load().ecc_msm_set_reduce_chunk(curve, log2_n, log2_chunk))
 
 
 def ecc_bench_imad(threads, iters, sink, stream=None):

@@ -113,13 +113,15 @@ def _carry_heavy(q, n, seed):
     return out
 
 
-def test_fp_mul_p256_special_form(gpu_lib):
-    """The P-256 base-field unit operations use the special-form reduction of
-    Section 4.2 (u = T_0, u q by additions): every product against the oracle on
-    operands chosen to stress its carries."""
+@pytest.mark.parametrize("cid", [1, 0], ids=["P-256", "secp256k1"])
+def test_fp_mul_special_form(gpu_lib, cid):
+    """The P-256 and secp256k1 base-field unit operations use the special-form
+    reductions of Section 4.2 (P-256: u = T_0, u q by additions; secp256k1:
+    u q = u 2^256 - u (2^32 + 977)): every product against the oracle on
+    operands chosen to stress their carries and borrows."""
     import torch
 
-    cid, q = 1, curves.P256.p
+    q = curves.BY_ID[cid].p
     n = 8192
     A, B = _carry_heavy(q, n, 11), _carry_heavy(q, n, 12)
     a, b = to_cuda(synth.ints_to_limbs(A, 8)), to_cuda(synth.ints_to_limbs(B, 8))
@@ -136,6 +138,7 @@ def test_bench_modmul_reductions(gpu_lib):
 
     sink = torch.zeros(512, dtype=torch.int32, device="cuda")
     gpu_lib.ecc_bench_modmul(1, 1, 512, 4, sink)
+    gpu_lib.ecc_bench_modmul(0, 1, 512, 4, sink)
     gpu_lib.ecc_bench_modmul(3, 0, 512, 4, sink)
     torch.cuda.synchronize()
     with pytest.raises(ecc.EccError):

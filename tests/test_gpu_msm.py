@@ -128,6 +128,28 @@ def test_msm_window_override_same_result(gpu_lib):
     gpu_lib.ecc_msm_set_window(cid, 9, 0)
 
 
+@pytest.mark.parametrize("cid", [2, 3])
+def test_msm_reduce_chunk_override_same_result(gpu_lib, cid):
+    """The bucket layout of the reduction (first-level chunks of 2^k buckets)
+    changes the rounds, never the sum: every k against the oracle, with
+    several window widths so chunks straddle or exceed a bucket row."""
+    C = curves.BY_ID[cid]
+    pts, _ = random_points(C, 700, 0x6ECC1800 + cid)
+    _, ks = synth.msm_raw(0x6ECC1900 + cid, 700, C.n, 1)
+    pts_l = _pts_limbs(C, pts)
+    want = _oracle_msm(cid, pts_l, ks[0])
+    try:
+        for c in (4, 9):
+            gpu_lib.ecc_msm_set_window(cid, 9, c)
+            for k in (1, 2, 3, 5, 7, 10):
+                gpu_lib.ecc_msm_set_reduce_chunk(cid, 9, k)
+                assert gpu_lib.ecc_msm_reduce_chunk(cid, 700) == k
+                assert _gpu_msm(gpu_lib, cid, pts_l, ks[0]) == want, (c, k)
+    finally:
+        gpu_lib.ecc_msm_set_window(cid, 9, 0)
+        gpu_lib.ecc_msm_set_reduce_chunk(cid, 9, 0)
+
+
 def test_msm_unsupported_curve(gpu_lib):
     import torch
 
