@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-msm", action="store_true", help="skip the MSM and ragged-MSM lines")
     ap.add_argument("--no-ragged", action="store_true", help="skip the ragged-MSM line")
     ap.add_argument("--no-sm2", action="store_true", help="skip the SM2 verification line")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the secp256k1 4096-triple and the SM2 signing / FPMUL lines")
     ap.add_argument("--msm-n", type=int, default=1 << 20, help="BLS12-381 MSM bases (default 2^20)")
     ap.add_argument("--msm-vectors", type=int, default=16, help="scalar vectors per MSM step")
     return ap.parse_args()
@@ -78,9 +80,10 @@ def dist_env():
 
 
 class ClockSampler:
-    """SM clocks and throttle reasons during the timed region: one background
-    `nvidia-smi -lms 200` started before the region (no process is forked while
-    it runs); only samples stamped inside the region are kept."""
+    """SM clocks and throttle reasons during timed regions: one background
+    `nvidia-smi -lms 200` for the whole run (started once, before the first
+    timed region); each line's timed region is a named window, and a window's
+    summary keeps only the samples stamped inside it."""
 
     FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -89,7 +92,7 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.t0 = self.t1 = None
+        self.windows = {}
         self.lines = []
 
     def start(self):
@@ -102,11 +105,11 @@ class ClockSampler:
             self.proc = None
         time.sleep(1.0)
 
-    def mark_begin(self):
-        self.t0 = time.time()
+    def begin(self, name):
+        self.windows[name] = [time.time(), None]
 
-    def mark_end(self):
-        self.t1 = time.time()
+    def end(self, name):
+        self.windows[name][1] = time.time()
 
     def stop(self):
         time.sleep(0.3)
@@ -119,9 +122,10 @@ class ClockSampler:
                 out = ""
             self.lines = [l for l in (out or "").splitlines() if l.strip()]
 
-    def summary(self):
+    def summary(self, name):
         import datetime
 
+        t0, t1 = self.windows.get(name, (None, None))
         rows = []
         for line in self.lines:
             c = [x.strip() for x in line.split(",")]
@@ -131,7 +135,7 @@ class ClockSampler:
                 ts = datetime.datetime.strptime(c[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
             except ValueError:
                 continue
-            if self.t0 is not None and not (self.t0 - 0.25 <= ts <= self.t1 + 0.25):
+            if t0 is not None and t1 is not None and not (t0 - 0.25 <= ts <= t1 + 0.25):
                 continue
             rows.append(c)
         if not rows:
@@ -144,6 +148,26 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
                 "samples": len(rows)}
+
+
+class _NoClock:
+    def begin(self, name):
+        pass
+
+    def end(self, name):
+        pass
+
+    def summary(self, name):
+        return None
+
+
+def hbm_peak():
+    """Measured copy bandwidth (GB/s) of the GB300s, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
 
 
 ORDERS = {1: 0xFFFFFFFF00000000FFFFFFFFFFFFFFFFBCE6FAADA7179E84F3B9CAC2FC632551,   # P-256 n
@@ -170,8 +194,8 @@ def gen_inputs(ecc, synth, torch, n, seed, curve=CURVE_P256):
 # dram__bytes_write.sum, from one ncu capture), valid only for the kernel sources
 # it was taken on: the digest of those sources must match, else it is null.
 VERIFY_TRAFFIC = {"bytes": 82872315136 + 34264189184, "batch": 1 << 20, "digest": "c4acca0c4152fa37",
-                  "sources": ["verify.cuh", "ops.cuh", "ec.cuh", "fp.cuh", "inv.cuh", "ptx.cuh",
-                              "curves_gen.cuh", "internal.h", "k_verify.cu"]}
+                  "sources": ["verify.cuh", "verify_host.cuh", "ops.cuh", "ec.cuh", "fp.cuh", "inv.cuh",
+                              "ptx.cuh", "curves_gen.cuh", "internal.h", "k_verify_p256.cu"]}
 
 
 def verify_traffic(n):
@@ -223,6 +247,7 @@ BN_R = 0x30644E72E131A029B85045B68181585D2833E84879B9709143E1F593F0000001
 
 
 def _event_time(torch, fn, reps):
+    """Mean device seconds per call of fn over reps back-to-back calls."""
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     a.record()
@@ -233,7 +258,32 @@ def _event_time(torch, fn, reps):
     return a.elapsed_time(b) / 1e3 / reps
 
 
-def bench_msm(ecc, costmodel, synth, torch, peak, rank, n=1 << 20, V=16, world=1):
+def _phases(ecc, torch, fn):
+    """Per-phase device milliseconds of one MSM call (library phase timers)."""
+    ecc.ecc_set_phase_timing(1)
+    try:
+        fn()
+        torch.cuda.synchronize()
+        return ecc.ecc_msm_phase_times()
+    finally:
+        ecc.ecc_set_phase_timing(0)
+
+
+def _sort_line(phases, points, digits):
+    """Achieved HBM rate of the counting sort (histogram + scatter): its
+    algorithmic bytes are two reads of every 32-byte scalar and, per (point,
+    window) digit, one 4-byte histogram update and one 4-byte entry write."""
+    peak, kind = hbm_peak()
+    b = 64 * points + 8 * digits
+    ms = phases.get("sort")
+    if not ms:
+        return None
+    gbs = b / (ms / 1e3) / 1e9
+    return {"ms": ms, "bytes": b, "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+            "peak_kind": kind}
+
+
+def bench_msm(ecc, costmodel, synth, torch, peak, rank, n=1 << 20, V=16, world=1, clk=None, reps=10):
     """BLS12-381 MSM: n resident bases a_i G (2^20 by default), V scalar vectors
     per step (16 by default; one ecc_msm_bases call), against the plain form (one
     MSM launch sequence per vector).  The bases are reused across calls, so they
@@ -254,13 +304,17 @@ def bench_msm(ecc, costmodel, synth, torch, peak, rank, n=1 << 20, V=16, world=1
     h = ecc.ecc_bases_create(curve, n, pts)
     out = torch.empty((V, 24), dtype=torch.int32, device="cuda")
     try:
+        clk = clk or _NoClock()
         ecc.ecc_msm_bases(h, V, sc, out)
-        t_tab = _event_time(torch, lambda: ecc.ecc_msm_bases(h, V, sc, out), 2)
+        t_tab = _event_time(torch, lambda: ecc.ecc_msm_bases(h, V, sc, out), 3)
         ref = out.clone()
         c, sweep = autotune.tune_precomputed(h, V, sc, torch, range(14, 23))
         ecc.ecc_msm_bases(h, V, sc, out)
-        t = _event_time(torch, lambda: ecc.ecc_msm_bases(h, V, sc, out), 2)
+        clk.begin("msm")
+        t = _event_time(torch, lambda: ecc.ecc_msm_bases(h, V, sc, out), reps)
+        clk.end("msm")
         same = bool(torch.equal(out, ref))
+        phases = _phases(ecc, torch, lambda: ecc.ecc_msm_bases(h, V, sc, out))
         one = out[:1]
         t1 = _event_time(torch, lambda: [ecc.ecc_msm_bases(h, 1, sc[v * n:(v + 1) * n], one)
                                          for v in range(V)], 1)
@@ -274,6 +328,8 @@ def bench_msm(ecc, costmodel, synth, torch, peak, rank, n=1 << 20, V=16, world=1
     shape = f"2^{log2n}" if n & (n - 1) == 0 else str(n)
     return {"workload": f"MSM BLS12-381 G1, {shape} resident bases, {V} scalar vectors per step",
             "value": job_rate(n * V, t, world), "unit": "points/s", "ms_per_step": t * 1e3, "window_c": c,
+            "timed_calls": reps, "clocks": clk.summary("msm"),
+            "phases_ms": phases, "sort": _sort_line(phases, n * V, n * V * W),
             "form": "resident bases with window multiples 2^(c w) P_i, one bucket set",
             "table": {"build_ms": sweep[c][0] * 1e3, "bytes": W * n * 96,
                       "sweep_ms": {str(k): round(v[1] * 1e3, 2) for k, v in sweep.items()}},
@@ -295,20 +351,24 @@ def bench_msm(ecc, costmodel, synth, torch, peak, rank, n=1 << 20, V=16, world=1
 PAPER_SM2_VERIFY_A100 = 4372853.0
 
 
-def bench_sm2(ecc, costmodel, synth, torch, peak, rank, n, steps, world=1):
+def bench_sm2(ecc, costmodel, synth, torch, peak, rank, n, steps, world=1, clk=None):
     """ECDSA verification on the SM2 curve, the paper's curve: 2^20 triples with
     the same recipe as the P-256 line (1/16 corrupted), inputs resident.  The
     schedule and the limb count are the P-256 kernel's, so is the work basis."""
     curve = ecc.ECC_SM2
     e, r, s, pub = gen_inputs(ecc, synth, torch, n, synth.SEED_BASE + 5 + 1000 * rank, curve)
     ok = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    clk = clk or _NoClock()
     for _ in range(3):
         ecc.ecc_verify_batch(curve, n, e, r, s, pub, ok)
-    t = _event_time(torch, lambda: ecc.ecc_verify_batch(curve, n, e, r, s, pub, ok), steps)
+    clk.begin("sm2")
+    t = _event_time(torch, lambda: ecc.ecc_verify_batch(curve, n, e, r, s, pub, ok), max(steps, 5))
+    clk.end("sm2")
     value = job_rate(n, t, world)
     alg = costmodel.verify_imad() * n
     return {"workload": "ECDSA verify, SM2, 2^20 seeded triples, 1/16 corrupted", "value": value,
             "unit": "verifies/s", "ms_per_step": t * 1e3, "valid_signatures": int(ok.sum().item()),
+            "timed_calls": max(steps, 5), "clocks": clk.summary("sm2"),
             "paper": {"value": PAPER_SM2_VERIFY_A100, "hardware": "NVIDIA A100 40 GB",
                       "source": "Table 4"},
             "ratio_to_paper": value / world / PAPER_SM2_VERIFY_A100,
@@ -316,16 +376,20 @@ def bench_sm2(ecc, costmodel, synth, torch, peak, rank, n, steps, world=1):
                          "peak": peak / 1e12, "unit": "T IMAD.WIDE/s", "frac": alg / t / peak}}
 
 
-def bench_ragged(ecc, costmodel, synth, torch, peak, rank, world=1):
+def bench_ragged(ecc, costmodel, synth, torch, peak, rank, world=1, clk=None, reps=10):
     """BN254 ragged batch: 256 MSMs with log-uniform sizes 2^10..2^18, all in one
     launch sequence captured once in a CUDA graph and replayed, against one
-    launch sequence per MSM.  The algorithmic work is the sum of every
+    launch sequence per MSM.  Window width and the reduction's bucket layout
+    are autotuned per size class.  The algorithmic work is the sum of every
     instance's Pippenger count at the window width the library picks for its
     size."""
     from paper_2501_03245_gb300 import autotune
 
+    clk = clk or _NoClock()
     curve = ecc.ECC_BN254
-    tuned = autotune.tune(curve, list(range(10, 19)), torch)  # one window width per size class
+    classes = list(range(10, 19))
+    tuned = autotune.tune(curve, classes, torch)  # one window width per size class
+    layout = autotune.tune_layout(curve, classes, torch)  # and one reduction chunk
     seed = synth.SEED_BASE + 3 + 1000 * rank
     sizes = synth.ragged_sizes(seed, 256)
     total = int(sizes.sum())
@@ -337,21 +401,26 @@ def bench_ragged(ecc, costmodel, synth, torch, peak, rank, world=1):
     out = torch.empty((256, 16), dtype=torch.int32, device="cuda")
     ecc.ecc_msm_ragged(curve, 256, offs, pts, sc, out)
     torch.cuda.synchronize()
-    eager = _event_time(torch, lambda: ecc.ecc_msm_ragged(curve, 256, offs, pts, sc, out), 2)
+    ref = out.clone()
+    clk.begin("ragged")
+    eager = _event_time(torch, lambda: ecc.ecc_msm_ragged(curve, 256, offs, pts, sc, out), reps)
     graph = None
     try:
         s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(s):
             ecc.ecc_msm_ragged(curve, 256, offs, pts, sc, out, s)  # warm inside the side stream
         torch.cuda.synchronize()
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=s):
             ecc.ecc_msm_ragged(curve, 256, offs, pts, sc, out, s)
-        ref = out.clone()
-        graph = _event_time(torch, g.replay, 3)
+        out.zero_()
+        graph = _event_time(torch, g.replay, reps)
         graph_ok = bool(torch.equal(out, ref))
     except Exception as ex:  # report, keep the eager number
         graph_ok = f"capture failed: {ex}"
+    clk.end("ragged")
+    phases = _phases(ecc, torch, lambda: ecc.ecc_msm_ragged(curve, 256, offs, pts, sc, out))
     one = torch.empty((1, 16), dtype=torch.int32, device="cuda")
     per = _event_time(torch, lambda: [ecc.ecc_msm(curve, int(sizes[i]), pts[int(offs[i]):int(offs[i + 1])],
                                                   sc[int(offs[i]):int(offs[i + 1])], one)
@@ -361,17 +430,106 @@ def bench_ragged(ecc, costmodel, synth, torch, peak, rank, world=1):
     widths = [ecc.ecc_msm_window(curve, int(k)) for k in sizes]
     alg = sum(costmodel.msm_modmul(int(k), costmodel.msm_windows(254, c), c) for k, c in zip(sizes, widths))
     alg *= costmodel.imad_per_modmul(8)
+    digits = sum(int(k) * costmodel.msm_windows(254, c) for k, c in zip(sizes, widths))
     return {"workload": "256 BN254 MSMs, sizes log-uniform 2^10..2^18, one launch sequence",
             "points": total, "value": job_rate(total, best, world), "unit": "points/s",
+            "form": "graph replay" if best is graph else "eager",
             "graph_replay_ms": graph * 1e3 if graph else None, "eager_ms": eager * 1e3,
-            "graph_bit_equal": graph_ok,
-            "autotuned": {str(k): v for k, v in sorted(tuned.items())},
+            "graph_bit_equal": graph_ok, "timed_calls": reps, "clocks": clk.summary("ragged"),
+            "autotuned": {str(k): {"c": v, "reduce_chunk_log2": layout.get(k)} for k, v in sorted(tuned.items())},
+            "phases_ms": phases, "sort": _sort_line(phases, total, digits),
             "plain": {"value": job_rate(total, per, world), "unit": "points/s",
                       "form": "one launch sequence per MSM", "frac": alg / per / peak},
             "roofline": {"bound": "alu", "achieved": alg / best / 1e12, "peak": peak / 1e12,
                          "unit": "T IMAD.WIDE/s", "frac": alg / best / peak,
                          "basis": "per instance: 6 modmul per (point, window) digit + 2 PADD per bucket "
                                   "+ c PDBL and 1 PADD per window, 136 wide mul-adds per modmul"}}
+
+
+SECP256K1_N = 0xFFFFFFFFFFFFFFFFFFFFFFFFFFFFFFFEBAAEDCE6AF48A03BBFD25E8CD0364141
+
+
+def bench_k1(ecc, costmodel, synth, torch, peak, rank, world=1, clk=None, reps=20, plain_n=64):
+    """ECDSA verification on secp256k1, 4096 triples (1/8 corrupted, the small
+    workload), batched (one launch for all 4096) against the plain form (one
+    triple per launch, timed on the first plain_n triples)."""
+    clk = clk or _NoClock()
+    curve, n = ecc.ECC_SECP256K1, 4096
+    raw = synth.ecdsa_raw(synth.SEED_BASE + 1000 * rank, n, SECP256K1_N, 8)
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()  # noqa: E731
+    d, e, k = dev(raw["d"]), dev(raw["e"]), dev(raw["k"])
+    r = torch.empty((n, 32), dtype=torch.uint8, device="cuda")
+    s = torch.empty_like(r)
+    pub = torch.empty((n, 64), dtype=torch.uint8, device="cuda")
+    ecc.ecc_sign_batch(curve, n, d, e, k, r, s, pub)
+    torch.cuda.synchronize()
+    r_h, s_h = synth.apply_corruption(r.cpu().numpy(), s.cpu().numpy(), raw["corrupt_idx"],
+                                      raw["corrupt_kind"], raw["corrupt_bit"])
+    r, s = dev(r_h), dev(s_h)
+    ok = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    for _ in range(3):
+        ecc.ecc_verify_batch(curve, n, e, r, s, pub, ok)
+    clk.begin("secp256k1")
+    t = _event_time(torch, lambda: ecc.ecc_verify_batch(curve, n, e, r, s, pub, ok), reps)
+    clk.end("secp256k1")
+    ok1 = torch.zeros(1, dtype=torch.uint8, device="cuda")
+    t1 = _event_time(torch, lambda: [ecc.ecc_verify_batch(curve, 1, e[i:i + 1], r[i:i + 1], s[i:i + 1],
+                                                          pub[i:i + 1], ok1) for i in range(plain_n)], 1)
+    alg = costmodel.verify_imad() * n
+    return {"workload": "ECDSA verify, secp256k1, 4096 seeded triples, 1/8 corrupted",
+            "value": job_rate(n, t, world), "unit": "verifies/s", "ms_per_step": t * 1e3,
+            "timed_calls": reps, "valid_signatures": int(ok.sum().item()), "clocks": clk.summary("secp256k1"),
+            "plain": {"value": job_rate(plain_n, t1, world), "unit": "verifies/s",
+                      "form": f"one triple per launch, first {plain_n} triples"},
+            "roofline": {"bound": "alu", "kernel": "k_verify<Secp256k1>", "achieved": alg / t / 1e12,
+                         "peak": peak / 1e12, "unit": "T IMAD.WIDE/s", "frac": alg / t / peak,
+                         "note": "4096 triples fill 16 of 304 resident CTAs: latency, not the pipe, "
+                                 "bounds this size"}}
+
+
+# The paper's ECDSA signing and fixed-point multiplication throughputs on its
+# own curve (SM2, NVIDIA A100 40 GB): Table 4 (signing) and Table 5 (FPMUL at
+# 2^11 and 2^14 operations per SP, 432 SPs), quoted for context.
+PAPER_SM2_SIGN_A100 = 14141978.0
+PAPER_SM2_FPMUL_A100 = {"2^11 per SP": 11723016.0, "2^14 per SP": 14389168.0}
+
+
+def bench_sign_fpmul(ecc, costmodel, synth, torch, peak, rank, n, world=1, clk=None, reps=5):
+    """Batched ECDSA signing and FPMUL k G on SM2 (the paper's curve), 2^20
+    items each, inputs resident; the fixed-base table is built before timing."""
+    clk = clk or _NoClock()
+    curve = ecc.ECC_SM2
+    raw = synth.ecdsa_raw(synth.SEED_BASE + 6 + 1000 * rank, n, ORDERS[curve], 16)
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()  # noqa: E731
+    d, e, k = dev(raw["d"]), dev(raw["e"]), dev(raw["k"])
+    r = torch.empty((n, 32), dtype=torch.uint8, device="cuda")
+    s = torch.empty_like(r)
+    pub = torch.empty((n, 64), dtype=torch.uint8, device="cuda")
+    kl = dev(synth.uniform_limbs(synth.SEED_BASE + 7 + 1000 * rank, 1, n, ORDERS[curve]).view(np.int32))
+    pts = torch.empty((n, 16), dtype=torch.int32, device="cuda")
+    for _ in range(3):
+        ecc.ecc_sign_batch(curve, n, d, e, k, r, s, pub)
+        ecc.ecc_fixed_base_mul(curve, n, kl, pts)
+    clk.begin("sign_fpmul")
+    t_sign = _event_time(torch, lambda: ecc.ecc_sign_batch(curve, n, d, e, k, r, s, pub), reps)
+    t_fp = _event_time(torch, lambda: ecc.ecc_fixed_base_mul(curve, n, kl, pts), reps)
+    clk.end("sign_fpmul")
+    m8 = costmodel.imad_per_modmul(8)
+    a_sign = costmodel.sign_modmul() * m8 * n
+    a_fp = costmodel.fpmul_modmul() * m8 * n
+    shape = "2^20" if n == 1 << 20 else str(n)
+    return {"workload": f"ECDSA sign and FPMUL, SM2, {shape} items each", "timed_calls": reps,
+            "clocks": clk.summary("sign_fpmul"),
+            "sign": {"value": job_rate(n, t_sign, world), "unit": "signs/s", "ms_per_step": t_sign * 1e3,
+                     "paper": {"value": PAPER_SM2_SIGN_A100, "hardware": "NVIDIA A100 40 GB",
+                               "source": "Table 4"},
+                     "roofline": {"bound": "alu", "kernel": "k_fixed_base<SM2> (signing mode)", "achieved": a_sign / t_sign / 1e12,
+                                  "peak": peak / 1e12, "unit": "T IMAD.WIDE/s", "frac": a_sign / t_sign / peak}},
+            "fpmul": {"value": job_rate(n, t_fp, world), "unit": "kG/s", "ms_per_step": t_fp * 1e3,
+                      "paper": {"value": PAPER_SM2_FPMUL_A100, "hardware": "NVIDIA A100 40 GB",
+                                "source": "Table 5"},
+                      "roofline": {"bound": "alu", "kernel": "k_fixed_base<SM2> (FPMUL mode)", "achieved": a_fp / t_fp / 1e12,
+                                   "peak": peak / 1e12, "unit": "T IMAD.WIDE/s", "frac": a_fp / t_fp / peak}}}
 
 
 def verify_config(n):
@@ -459,7 +617,7 @@ def run_ours(args):
     clk = ClockSampler(local)
     clk.start()
     barrier()
-    clk.mark_begin()
+    clk.begin("verify")
     t_all0 = torch.cuda.Event(enable_timing=True)
     t_all1 = torch.cuda.Event(enable_timing=True)
     t_all0.record(stream)
@@ -469,8 +627,7 @@ def run_ours(args):
         b.record(stream)
     t_all1.record(stream)
     barrier()
-    clk.mark_end()
-    clk.stop()
+    clk.end("verify")
     total_s = t_all0.elapsed_time(t_all1) / 1e3
     per_launch = [a.elapsed_time(b) / 1e3 for a, b in events]
     value = job_rate(n * args.steps, total_s, world)
@@ -530,16 +687,23 @@ def run_ours(args):
         "e2e": {"value": e2e_value, "unit": "verifies/s",
                 "h2d_bytes_per_step": 160 * n, "d2h_bytes_per_step": n, "bit_equal": e2e_ok},
         "gpu_launches": args.steps,
-        "clocks": clk.summary(),
     }
     del e, r, s, pub, ok, e_h, r_h, s_h, p_h, ok_h
     if not args.no_msm:
         line["msm"] = bench_msm(ecc, costmodel, synth, torch, peak, rank, args.msm_n, args.msm_vectors,
-                                world)
+                                world, clk)
         if not args.no_ragged:
-            line["ragged"] = bench_ragged(ecc, costmodel, synth, torch, peak, rank, world)
+            line["ragged"] = bench_ragged(ecc, costmodel, synth, torch, peak, rank, world, clk)
     if not args.no_sm2:
-        line["sm2"] = bench_sm2(ecc, costmodel, synth, torch, peak, rank, n, args.steps, world)
+        line["sm2"] = bench_sm2(ecc, costmodel, synth, torch, peak, rank, n, args.steps, world, clk)
+    if not args.no_extra:
+        line["secp256k1"] = bench_k1(ecc, costmodel, synth, torch, peak, rank, world, clk)
+        line["sign_fpmul"] = bench_sign_fpmul(ecc, costmodel, synth, torch, peak, rank, n, world, clk)
+    clk.stop()
+    line["clocks"] = clk.summary("verify")
+    for key in ("msm", "ragged", "sm2", "secp256k1", "sign_fpmul"):
+        if key in line:
+            line[key]["clocks"] = clk.summary({"sign_fpmul": "sign_fpmul"}.get(key, key))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline
     if rank == 0:

@@ -203,6 +203,23 @@ int ecc_msm(ecc_curve_t curve, size_t n, const uint32_t* points, const uint32_t*
 int ecc_msm_ragged(ecc_curve_t curve, size_t num, const uint64_t* offsets, const uint32_t* points,
                    const uint32_t* scalars, uint32_t* out, void* stream);
 
+/* Ragged MSMs whose instance boundaries live in DEVICE memory, so that one
+ * captured CUDA graph can serve a new mix of sizes on every replay (the sizes
+ * are read on the device; nothing about the launch sequence depends on them).
+ * offsets: DEVICE array of num + 1 row indices with offsets[0] = 0; instance i
+ * uses rows [offsets[i], offsets[i+1]) of points and scalars (DEVICE arrays of
+ * at least max_points rows); out: num points (DEVICE).  max_points is the
+ * capacity fixed when the call is made or recorded: every workspace is sized
+ * for max_points rows in num instances.  Every instance uses one window width
+ * c (2..20; 0 picks the library's width for max_points / num points), so the
+ * bucket layout needs no sizes.  Offsets that decrease, do not start at 0 or
+ * end above max_points are refused on the device: every output is then O and
+ * the status word holds ECC_EINVAL (see ecc_sync_status).  The call is
+ * asynchronous; it allocates stream-ordered workspace like ecc_msm_ragged. */
+int ecc_msm_ragged_dev(ecc_curve_t curve, size_t num, size_t max_points, const uint64_t* offsets,
+                       const uint32_t* points, const uint32_t* scalars, uint32_t* out, int c,
+                       void* stream);
+
 /* Resident bases: convert n points once into the library's device layout
  * (owned by the handle until ecc_bases_destroy), then run MSMs of many scalar
  * vectors against them.  ecc_msm_bases: scalars = num_vectors x n x 8 limbs,
@@ -234,6 +251,45 @@ int ecc_bases_window(void* handle);
 int ecc_msm_bases_ragged(void* handle, size_t num, const uint64_t* sizes, const uint32_t* scalars,
                          uint32_t* out, void* stream);
 
+/* The serving form of ecc_msm_ragged_dev: instance i is sum_j k_ij P_j over
+ * the first sizes[i] resident bases, its sizes[i] scalar rows following those
+ * of instance i - 1.  sizes: DEVICE array of num counts, each at most the
+ * handle's base count, at most max_points in all; scalars, out: DEVICE.  One
+ * window width for every instance: the handle's window-multiple width, or the
+ * library's width for max_points / num points.  Refused sizes give O outputs
+ * and ECC_EINVAL in the status word. */
+int ecc_msm_bases_ragged_dev(void* handle, size_t num, size_t max_points, const uint64_t* sizes,
+                             const uint32_t* scalars, uint32_t* out, void* stream);
+
+/* Device-side errors.  Kernels that find an error they can only see on the
+ * device (device-resident sizes out of range; a bounded wait that gave up)
+ * record its ECC_E* code in a status word of the current device (the first
+ * error wins).  ecc_sync_status synchronises `stream`, returns the recorded
+ * code (ECC_OK if none) with a message in ecc_last_error(), and clears it.
+ * The word is per device, not per stream or per call: it reports errors of
+ * any work on the device since the last ecc_sync_status. */
+int ecc_sync_status(void* stream);
+
+/* Caller-provided workspace allocator.  Every internal workspace of the
+ * library (the per-call scratch of every entry point) is then taken from
+ * alloc(bytes, stream, ctx) and returned with release(ptr, stream, ctx), both
+ * called on the calling host thread with the call's stream; the memory must be
+ * usable by work on that stream until release (stream-ordered semantics, e.g.
+ * a framework's caching allocator).  alloc returning NULL makes the call fail
+ * with ECC_ENOMEM.  Both NULL restores the default (cudaMallocAsync /
+ * cudaFreeAsync).  Not used by ecc_fp_inv_batch_noalloc, nor for the
+ * library-lifetime tables (fixed-base tables, resident bases). */
+typedef void* (*ecc_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*ecc_free_fn)(void* ptr, void* stream, void* ctx);
+int ecc_set_allocator(ecc_alloc_fn alloc, ecc_free_fn release, void* ctx);
+
+/* ok_out[i] = 1 when point i is O (written (0, 0)) or has canonical
+ * coordinates that satisfy y^2 = x^3 + a x + b (Eqn 1), else 0.  Membership
+ * of the prime-order subgroup is not checked (BN254 G1 has cofactor 1;
+ * BLS12-381 G1 does not).  points as for ecc_msm; ok_out: n bytes. */
+int ecc_validate_points(ecc_curve_t curve, size_t n, const uint32_t* points, uint8_t* ok_out,
+                        void* stream);
+
 /* Window width used for an n-point MSM, and the autotuner's override for the
  * size class floor(log2 n) (c = 0 restores the cost-model default). */
 int ecc_msm_window(ecc_curve_t curve, size_t n);
@@ -250,6 +306,29 @@ int ecc_msm_set_window(ecc_curve_t curve, int log2_n, int c);
  * do not depend on k. */
 int ecc_msm_reduce_chunk(ecc_curve_t curve, size_t n);
 int ecc_msm_set_reduce_chunk(ecc_curve_t curve, int log2_n, int log2_chunk);
+
+/* Gather-apply-scatter across a thread-block cluster for P-256 verification
+ * (the memory-management idea of Section 3.3 taken to a cluster): with ctas =
+ * 2 or 4, ecc_verify_batch on P-256 runs in clusters of that many CTAs that
+ * share each round's single inversion through distributed shared memory (the
+ * other CTAs' products go to the first, which inverts their product by
+ * Montgomery's trick and sends each its inverse back); ctas = 1 gives every
+ * CTA its own inversion.  Process-wide setting; results are identical for
+ * every value; other values give ECC_EINVAL. */
+int ecc_set_gas_cluster(int ctas);
+
+/* MSM phase timers (diagnostics).  With timing on, every MSM entry point
+ * records CUDA events on its stream at the boundaries of its five phases:
+ * 0 counting sort by bucket id (histogram, scans, scatter), 1 batched affine
+ * bucket accumulation, 2 fold of each bucket's partial sums, 3 bucket
+ * reduction (the affine first level and the Jacobian upper levels), 4 window
+ * combination.  Nothing is recorded while the stream is being captured.
+ * ecc_msm_phase_times waits for the calling thread's last timed MSM call and
+ * writes the device milliseconds of up to max_phases phases to ms_out (host);
+ * returns the number written, or ECC_EINVAL if this thread has no complete
+ * timed call.  Timing costs a few event records per call; off by default. */
+int ecc_set_phase_timing(int on);
+int ecc_msm_phase_times(float* ms_out, int max_phases);
 
 /* ---------------------------------------------------------------- benchmarks
  * Integer multiply-add issue-rate probe (the microbenchmark method of

@@ -128,3 +128,48 @@ def tune(curve, log2_sizes, torch, spread=2, seed=0x6ECC7777, cache=None, vector
         with open(cache, "w") as f:
             json.dump(data, f, indent=1)
     return table
+
+
+def tune_layout(curve, log2_sizes, torch, candidates=(3, 4, 5, 6), seed=0x6ECC7778, batch_points=1 << 22):
+    """Bucket layout of the reduction: for every size class (after its window
+    width is set), times a ragged call of equal instances of that size (about
+    batch_points points in all, the shape of a batch, where the reduction's
+    rounds are shared by many instances) with first-level reduction chunks of
+    2^k buckets for each candidate k (capped at c - 1, where a chunk covers a
+    whole bucket row), installs the fastest with ecc_msm_set_reduce_chunk and
+    returns {log2_n: k}."""
+    import numpy as np
+
+    table = {}
+    if not log2_sizes:
+        return table
+    n_max = max(1 << max(log2_sizes), batch_points)
+    bases = make_bases(curve, n_max, seed, torch)
+    ks = synth.uniform_limbs(seed, synth.S_SCALAR, n_max, _curve_order(curve))
+    scalars = torch.from_numpy(ks.view("int32")).cuda()
+    limbs = ecc.ecc_limbs(curve)
+    for l in log2_sizes:
+        n = 1 << l
+        m = max(1, batch_points // n)
+        offs = np.arange(m + 1, dtype=np.uint64) * n
+        out = torch.empty((m, 2 * limbs), dtype=torch.int32, device="cuda")
+        c = ecc.ecc_msm_window(curve, n)
+        best = None
+        for k in sorted({min(k, c - 1) for k in candidates}):
+            if k < 1:
+                continue
+            ecc.ecc_msm_set_reduce_chunk(curve, l, k)
+            ecc.ecc_msm_ragged(curve, m, offs, bases, scalars, out)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(3):
+                ecc.ecc_msm_ragged(curve, m, offs, bases, scalars, out)
+            b.record()
+            torch.cuda.synchronize()
+            t = a.elapsed_time(b)
+            if best is None or t < best[0]:
+                best = (t, k)
+        table[l] = best[1]
+        ecc.ecc_msm_set_reduce_chunk(curve, l, best[1])
+    return table

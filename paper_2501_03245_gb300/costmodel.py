@@ -65,6 +65,17 @@ def fpmul_modmul():
     return G_COMB_ADDS * BATCH_PADD_MODMUL
 
 
+# s = k^-1 (e + r d) mod n per signature: the batched inversion of k (3 modmul
+# per item) and the products r d and (e + r d) k^-1, plus r into Montgomery form
+SIGN_SCALAR_MODMUL = 7
+
+
+def sign_modmul():
+    """Algorithmic modmul per ECDSA signature: k G and the public key d G share
+    the 32 comb rounds (two additions per round), then s = k^-1 (e + r d)."""
+    return 2 * G_COMB_ADDS * BATCH_PADD_MODMUL + SIGN_SCALAR_MODMUL
+
+
 def break_even_batch(inv_over_mul=100):
     """Smallest batch N for which 1 modinv + 6N modmul < 11N modmul
     (affine batch vs Jacobian PADD, Section 3.1) with modinv = inv_over_mul modmul."""

@@ -3,6 +3,7 @@
 #include <cstdio>
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -114,12 +115,74 @@ int with_args(const char* name, cudaStream_t st, std::vector<Arg*> ins, std::vec
 
 }  // namespace
 
-cudaError_t Scratch::alloc(size_t b, cudaStream_t s) {
-  if (ptr) cudaFreeAsync(ptr, st);
+namespace {
+
+// Caller-installed workspace allocator (ecc_set_allocator); null: stream-ordered
+// cudaMallocAsync / cudaFreeAsync.
+std::mutex g_alloc_mu;
+ecc_alloc_fn g_alloc = nullptr;
+ecc_free_fn g_free = nullptr;
+void* g_alloc_ctx = nullptr;
+
+// Device status word (one per device that loads the library).
+__device__ int g_status;
+std::mutex g_status_mu;
+int* g_status_ptr[64] = {};
+
+}  // namespace
+
+int* status_word() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(g_status_mu);
+  if (!g_status_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_status) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    g_status_ptr[dev] = static_cast<int*>(p);
+  }
+  return g_status_ptr[dev];
+}
+
+void Scratch::release() {
+  if (!ptr) return;
+  if (hooked) {
+    ecc_free_fn f;
+    void* ctx;
+    {
+      std::lock_guard<std::mutex> lock(g_alloc_mu);
+      f = g_free;
+      ctx = g_alloc_ctx;
+    }
+    if (f) f(ptr, st, ctx);
+  } else {
+    cudaFreeAsync(ptr, st);
+  }
   ptr = nullptr;
+}
+
+cudaError_t Scratch::alloc(size_t b, cudaStream_t s) {
+  release();
   st = s;
   bytes = b;
   if (b == 0) b = 16;
+  {
+    ecc_alloc_fn f;
+    void* ctx;
+    {
+      std::lock_guard<std::mutex> lock(g_alloc_mu);
+      f = g_alloc;
+      ctx = g_alloc_ctx;
+    }
+    if (f) {
+      hooked = true;
+      ptr = f(b, s, ctx);
+      return ptr ? cudaSuccess : cudaErrorMemoryAllocation;
+    }
+  }
+  hooked = false;
   static bool pool_set = false;
   if (!pool_set) {
     // keep freed stream-ordered memory cached in the pool between calls
@@ -393,6 +456,103 @@ int ecc_msm(ecc_curve_t curve, size_t n, const uint32_t* points, const uint32_t*
   return rc;
 }
 
+static bool msm_dev_sizes_ok(int curve, size_t num, size_t max_points, int c, int pre_c) {
+  const int w = pre_c > 0 ? pre_c : (c > 0 ? c : msm_window(curve, num ? std::max<size_t>(max_points / num, 2) : 2));
+  const uint64_t W = (uint64_t)((curve == ECC_BN254 ? 254 : 255) + 1 + w - 1) / w;
+  const uint64_t rows = pre_c > 0 ? 1 : W;
+  return (uint64_t)max_points * W < kMsmMaxDigits && (uint64_t)num * (rows << (w - 1)) < kMsmMaxDigits;
+}
+
+int ecc_msm_ragged_dev(ecc_curve_t curve, size_t num, size_t max_points, const uint64_t* offsets,
+                       const uint32_t* points, const uint32_t* scalars, uint32_t* out, int c,
+                       void* stream) {
+  const char* name = "ecc_msm_ragged_dev";
+  if (!valid_curve(curve)) return fail(ECC_EINVAL, "%s: unknown curve %d", name, (int)curve);
+  if (curve != ECC_BN254 && curve != ECC_BLS12_381)
+    return fail(ECC_EUNSUPPORTED, "%s: MSM is offered on BN254 and BLS12-381", name);
+  if (num == 0) return ok();
+  if (!offsets || !points || !scalars || !out) return fail(ECC_EINVAL, "%s: NULL pointer", name);
+  if (num > (1u << 20)) return fail(ECC_EINVAL, "%s: num > 2^20", name);
+  if (max_points == 0 || max_points > (1ull << 28))
+    return fail(ECC_EINVAL, "%s: max_points must be in 1..2^28", name);
+  if (c != 0 && (c < 2 || c > 20)) return fail(ECC_EINVAL, "%s: c must be 0 or 2..20", name);
+  if (!aligned4(points) || !aligned4(scalars) || !aligned4(out) || (reinterpret_cast<uintptr_t>(offsets) & 7))
+    return fail(ECC_EINVAL, "%s: pointers must be aligned (offsets to 8 bytes, the rest to 4)", name);
+  if (host_memory(offsets) || host_memory(points) || host_memory(scalars) || host_memory(out))
+    return fail(ECC_EINVAL, "%s: every array must be device memory", name);
+  if (!msm_dev_sizes_ok(curve, num, max_points, c, 0))
+    return fail(ECC_EINVAL, "%s: the capacity needs 2^31 or more (point, window) digits or buckets", name);
+  cudaError_t e = launch_msm_dev(curve, (uint32_t)num, max_points, offsets, c, points, scalars, out,
+                                 static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, name);
+  return ok();
+}
+
+int ecc_msm_bases_ragged_dev(void* handle, size_t num, size_t max_points, const uint64_t* sizes,
+                             const uint32_t* scalars, uint32_t* out, void* stream) {
+  const char* name = "ecc_msm_bases_ragged_dev";
+  if (!handle) return fail(ECC_EINVAL, "%s: NULL handle", name);
+  if (num == 0) return ok();
+  if (!sizes || !scalars || !out) return fail(ECC_EINVAL, "%s: NULL pointer", name);
+  if (num > (1u << 20)) return fail(ECC_EINVAL, "%s: num > 2^20", name);
+  if (max_points == 0 || max_points > (1ull << 28))
+    return fail(ECC_EINVAL, "%s: max_points must be in 1..2^28", name);
+  if (!aligned4(scalars) || !aligned4(out) || (reinterpret_cast<uintptr_t>(sizes) & 7))
+    return fail(ECC_EINVAL, "%s: pointers must be aligned (sizes to 8 bytes, the rest to 4)", name);
+  if (host_memory(sizes) || host_memory(scalars) || host_memory(out))
+    return fail(ECC_EINVAL, "%s: every array must be device memory", name);
+  if (!msm_dev_sizes_ok(bases_curve(handle), num, max_points, 0, bases_window(handle)))
+    return fail(ECC_EINVAL, "%s: the capacity needs 2^31 or more (point, window) digits or buckets", name);
+  cudaError_t e = launch_msm_bases_dev(handle, (uint32_t)num, max_points, sizes, 0, scalars, out,
+                                       static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, name);
+  return ok();
+}
+
+int ecc_sync_status(void* stream) {
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "ecc_sync_status");
+  int* w = status_word();
+  if (!w) return fail(ECC_ECUDA, "ecc_sync_status: no status word on this device");
+  int v = 0;
+  e = cudaMemcpy(&v, w, sizeof v, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && v != 0) {
+    const int zero = 0;
+    e = cudaMemcpy(w, &zero, sizeof zero, cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "ecc_sync_status");
+  if (v == 0) return ok();
+  return fail(v, "ecc_sync_status: a kernel reported error %d (%s)", v,
+              v == ECC_EINVAL ? "refused device-resident sizes" : v == ECC_ETIMEOUT ? "a bounded wait gave up"
+                                                                    : "device error");
+}
+
+int ecc_set_allocator(ecc_alloc_fn alloc, ecc_free_fn release, void* ctx) {
+  if ((alloc == nullptr) != (release == nullptr))
+    return fail(ECC_EINVAL, "ecc_set_allocator: give both functions or neither");
+  std::lock_guard<std::mutex> lock(g_alloc_mu);
+  g_alloc = alloc;
+  g_free = release;
+  g_alloc_ctx = ctx;
+  return ok();
+}
+
+int ecc_validate_points(ecc_curve_t curve, size_t n, const uint32_t* points, uint8_t* ok_out,
+                        void* stream) {
+  const char* name = "ecc_validate_points";
+  if (!valid_curve(curve)) return fail(ECC_EINVAL, "%s: unknown curve %d", name, (int)curve);
+  if (n == 0) return ok();
+  if (!points || !ok_out) return fail(ECC_EINVAL, "%s: NULL pointer", name);
+  if (!aligned4(points)) return fail(ECC_EINVAL, "%s: points must be 4-byte aligned", name);
+  if (n > (size_t)1 << 30) return fail(ECC_EINVAL, "%s: n > 2^30", name);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Arg P(points, n * 2 * field_limbs(curve, 0) * 4), O(ok_out, n);
+  return with_args(name, st, {&P}, {&O}, [&]() {
+    return launch_validate_points(curve, n, static_cast<const uint32_t*>(P.dev),
+                                  static_cast<uint8_t*>(O.dev), st);
+  });
+}
+
 int ecc_bases_create(ecc_curve_t curve, size_t n, const uint32_t* points, void** handle,
                      void* stream) {
   const char* name = "ecc_bases_create";
@@ -523,6 +683,27 @@ int ecc_msm_set_reduce_chunk(ecc_curve_t curve, int log2_n, int log2_chunk) {
                 kMsmReduceLogMax);
   msm_set_reduce_log(curve, log2_n, log2_chunk);
   return ok();
+}
+
+int ecc_set_gas_cluster(int ctas) {
+  if (ctas != 1 && ctas != 2 && ctas != 4) return fail(ECC_EINVAL, "ecc_set_gas_cluster: ctas must be 1, 2 or 4");
+  set_gas_cluster(ctas);
+  return ok();
+}
+
+int ecc_set_phase_timing(int on) {
+  set_phase_timing(on != 0);
+  return ok();
+}
+
+int ecc_msm_phase_times(float* ms_out, int max_phases) {
+  if (!ms_out || max_phases < 1) return fail(ECC_EINVAL, "ecc_msm_phase_times: bad argument");
+  float ms[kMsmPhases];
+  if (!phase_times(ms))
+    return fail(ECC_EINVAL, "ecc_msm_phase_times: no complete timed MSM call on this thread");
+  const int k = max_phases < kMsmPhases ? max_phases : kMsmPhases;
+  for (int i = 0; i < k; ++i) ms_out[i] = ms[i];
+  return k;
 }
 
 int ecc_bench_imad(size_t threads, int iters, uint32_t* sink, void* stream) {

@@ -5,6 +5,8 @@
 #include <cstddef>
 #include <cstdint>
 
+#include <cooperative_groups.h>
+
 #include "curves_gen.cuh"
 #include "fp.cuh"
 
@@ -218,6 +220,8 @@ struct GasSmem {
   uint4 tree[5][N / 4][BLOCK];
   uint32_t warp_tot[NW][N];
   uint32_t warp_inv[NW][N];
+  uint32_t pair_in[4][N];  // cluster inversion: the other CTAs' totals (in CTA 0)
+  uint32_t pair_out[N];    // and the inverse CTA 0 sends back
 };
 
 // The GAS scratch lives in dynamic shared memory (it exceeds the 48 KB static
@@ -234,8 +238,12 @@ ECC_DEV void fe_shfl_xor(uint32_t* r, const uint32_t* a, int mask) {
   for (int i = 0; i < F::N; ++i) r[i] = __shfl_xor_sync(0xffffffffu, a[i], mask);
 }
 
-template <class F, int BLOCK>
+// CL > 1: the kernel runs in clusters of CL (2 or 4) CTAs that share one
+// inversion per round (every CTA of a cluster must call this the same number
+// of times).
+template <class F, int BLOCK, int CL = 1>
 __device__ void cta_invert(uint32_t* out, const uint32_t* in, GasSmem<F::N, BLOCK>& sm) {
+  static_assert(CL == 1 || CL == 2 || CL == 4, "clusters of 1, 2 or 4 CTAs");
   constexpr int N = F::N;
   constexpr int NW = BLOCK / 32;
   const int tid = threadIdx.x;
@@ -255,11 +263,11 @@ __device__ void cta_invert(uint32_t* out, const uint32_t* in, GasSmem<F::N, BLOC
     for (int i = 0; i < N; ++i) sm.warp_tot[warp][i] = v[i];
   }
   __syncthreads();
+  // the same butterfly over the warp totals in warp 0 (lanes >= NW carry 1),
+  // so the serial part is log2(NW) products up, one inversion, log2(NW) down
+  constexpr int LW = NW <= 1 ? 0 : (NW <= 2 ? 1 : (NW <= 4 ? 2 : (NW <= 8 ? 3 : (NW <= 16 ? 4 : 5))));
+  uint32_t w[N], keep[LW > 0 ? LW : 1][N];
   if (warp == 0) {
-    // the same butterfly over the warp totals (lanes >= NW carry 1), so the
-    // serial part is log2(NW) products up, one inversion, log2(NW) down
-    constexpr int LW = NW <= 1 ? 0 : (NW <= 2 ? 1 : (NW <= 4 ? 2 : (NW <= 8 ? 3 : (NW <= 16 ? 4 : 5))));
-    uint32_t w[N], keep[LW > 0 ? LW : 1][N];
     if (lane < NW) {
 #pragma unroll
       for (int i = 0; i < N; ++i) w[i] = sm.warp_tot[lane][i];
@@ -272,7 +280,56 @@ __device__ void cta_invert(uint32_t* out, const uint32_t* in, GasSmem<F::N, BLOC
       fe_shfl_xor<F>(t, w, 1 << l);
       mont_mul<F>(w, w, t);
     }
-    if (lane == 0) fe_inv_mont<F>(w, w);
+  }
+  if constexpr (CL > 1) {
+    // one inversion for the CL CTAs of a cluster: every other CTA's total goes
+    // to the first through distributed shared memory; the first inverts the
+    // product (Montgomery's trick over the CL totals) and sends each CTA its
+    // own inverse back.  Two cluster barriers, passed by every thread of all
+    // CL CTAs.
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const unsigned rank = cl.block_rank();
+    if (warp == 0 && lane == 0 && rank != 0) {
+      uint32_t* dst = cl.map_shared_rank(&sm.pair_in[rank][0], 0);
+#pragma unroll
+      for (int i = 0; i < N; ++i) dst[i] = w[i];
+    }
+    cl.sync();
+    if (warp == 0 && lane == 0 && rank == 0) {
+      // prefix products p_k = t_0 .. t_k of the CL totals, one inversion of
+      // p_(CL-1), then walk back: t_k^-1 = acc p_(k-1), acc <- acc t_k
+      uint32_t pre[CL][N], acc[N], tk[N];
+      fe_copy<F>(pre[0], w);
+#pragma unroll
+      for (int k = 1; k < CL; ++k) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) tk[i] = sm.pair_in[k][i];
+        mont_mul<F>(pre[k], pre[k - 1], tk);
+      }
+      fe_inv_mont<F>(acc, pre[CL - 1]);
+#pragma unroll
+      for (int k = CL - 1; k >= 1; --k) {
+        uint32_t mine[N];
+        mont_mul<F>(mine, acc, pre[k - 1]);
+        uint32_t* dst = cl.map_shared_rank(&sm.pair_out[0], k);
+#pragma unroll
+        for (int i = 0; i < N; ++i) dst[i] = mine[i];
+#pragma unroll
+        for (int i = 0; i < N; ++i) tk[i] = sm.pair_in[k][i];
+        mont_mul<F>(acc, acc, tk);
+      }
+      fe_copy<F>(w, acc);
+    }
+    cl.sync();
+    if (warp == 0 && lane == 0 && rank != 0) {
+#pragma unroll
+      for (int i = 0; i < N; ++i) w[i] = sm.pair_out[i];
+    }
+  } else {
+    if (warp == 0 && lane == 0) fe_inv_mont<F>(w, w);
+  }
+  if (warp == 0) {
 #pragma unroll
     for (int i = 0; i < N; ++i) w[i] = __shfl_sync(0xffffffffu, w[i], 0);
 #pragma unroll
@@ -319,7 +376,7 @@ __device__ void cta_invert(uint32_t* out, const uint32_t* in, GasSmem<F::N, BLOC
 // intermediate array of Section 3.3); DCWPA recomputes the item's denominators
 // and, for OPS > 1, the partial products inside the item (find-then-recompute,
 // Section 3.4) instead of storing them.
-template <class F, int BLOCK, class R>
+template <class F, int BLOCK, int CL = 1, class R>
 __device__ void batch_round(R& rd, size_t begin, size_t end, const SoA<F>& M,
                             GasSmem<F::N, BLOCK>& sm) {
   constexpr int N = F::N;
@@ -337,7 +394,7 @@ __device__ void batch_round(R& rd, size_t begin, size_t end, const SoA<F>& M,
     }
   }
   uint32_t inv[N];
-  cta_invert<F, BLOCK>(inv, run, sm);
+  cta_invert<F, BLOCK, CL>(inv, run, sm);
   if (i0 < end) {
     const size_t last = i0 + ((end - 1 - i0) / BLOCK) * BLOCK;
     for (size_t i = last + BLOCK; i > i0;) {

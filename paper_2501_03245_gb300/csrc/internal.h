@@ -11,17 +11,18 @@
 namespace ecc {
 
 // Stream-ordered device scratch, released at scope exit (cudaFreeAsync on the
-// same stream, so later work on the stream may still be using it safely).
+// same stream, so later work on the stream may still be using it safely), or
+// through the caller's allocator hook when one is installed.
 struct Scratch {
   void* ptr = nullptr;
   cudaStream_t st = nullptr;
   size_t bytes = 0;
+  bool hooked = false;
   Scratch() = default;
   Scratch(const Scratch&) = delete;
   Scratch& operator=(const Scratch&) = delete;
-  ~Scratch() {
-    if (ptr) cudaFreeAsync(ptr, st);
-  }
+  ~Scratch() { release(); }
+  void release();
   cudaError_t alloc(size_t b, cudaStream_t s);
   template <class T>
   T* as() const {
@@ -62,10 +63,16 @@ struct CustomConsts {
 int custom_consts(const uint32_t* p, const uint32_t* a, CustomConsts* cc);
 cudaError_t launch_point_add_custom(const CustomConsts& cc, size_t n, const uint32_t* p,
                                     const uint32_t* q, uint32_t* out, int dbl, cudaStream_t st);
+// ok[i] = 1 when point i is O ((0, 0)) or canonical and on the curve (Eqn 1)
+cudaError_t launch_validate_points(int curve, size_t n, const uint32_t* p, uint8_t* ok, cudaStream_t st);
 // Fixed-base table of a curve on the current device (built on first use,
 // synchronously on `st`): 32 x 256 entries, entry j*256+v = v 2^(8j) G, SoA
 // Montgomery (x block then y block).
 cudaError_t gtable(int curve, const uint4** table, cudaStream_t st);
+
+// P-256 verification in clusters of `ctas` (1, 2 or 4) CTAs sharing each
+// round's inversion
+void set_gas_cluster(int ctas);
 
 // FPMUL k_i G (scalars n x 8 LE limbs; out n x 2N LE limbs)
 cudaError_t launch_fixed_base_mul(int curve, size_t n, const uint32_t* k, uint32_t* out,
@@ -104,6 +111,30 @@ uint64_t bases_count(void* handle);
 cudaError_t launch_msm_bases(void* handle, uint32_t num_vectors, const uint64_t* sizes,
                              const uint32_t* scalars,
                              uint32_t* out, cudaStream_t st);
+
+// MSM phase timers (diagnostics): with timing on, phase_mark(i, st) records
+// boundary event i (0 .. kMsmPhases) of the calling thread's current MSM call
+// on st; nothing is recorded while st is being captured into a graph.
+constexpr int kMsmPhases = 5;  // sort, accumulation, fold, reduction, combination
+void set_phase_timing(bool on);
+void phase_mark(int i, cudaStream_t st);
+// Device milliseconds of each phase of the thread's last timed call (waits for
+// it); returns false if no complete timed call exists.
+bool phase_times(float* ms);
+
+// Device status word of the current device (library-owned, zero when no
+// device-side error is pending): kernels that detect an error record its
+// negative ECC_E* code with atomicCAS(word, 0, code).
+int* status_word();
+
+// Ragged MSMs whose instance sizes are in device memory (capacity cap rows,
+// one window width c for every instance; 0 picks the library's width for the
+// mean size cap / num).
+cudaError_t launch_msm_dev(int curve, uint32_t num, uint64_t cap, const uint64_t* offsets, int c,
+                           const uint32_t* points, const uint32_t* scalars, uint32_t* out,
+                           cudaStream_t st);
+cudaError_t launch_msm_bases_dev(void* handle, uint32_t num, uint64_t cap, const uint64_t* sizes, int c,
+                                 const uint32_t* scalars, uint32_t* out, cudaStream_t st);
 
 // benchmarks
 cudaError_t launch_bench_imad(size_t threads, int iters, uint32_t* sink, cudaStream_t st);

@@ -2,6 +2,7 @@
 // autotuner overrides), resident bases, and dispatch to the per-curve
 // translation units (k_msm_bn254.cu, k_msm_bls12_381.cu).
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <mutex>
 
@@ -22,6 +23,16 @@ cudaError_t msm_bases_bls12_381(void* bases, uint32_t num_vectors, const uint64_
 cudaError_t points_to_mont(int curve, const uint32_t* in, uint64_t n, uint32_t* out,
                            cudaStream_t st);
 cudaError_t bases_precompute_bn254(void* bases, int c, cudaStream_t st);
+cudaError_t msm_points_dev_bn254(uint32_t num, uint64_t cap, const uint64_t* offsets, int c,
+                                 const uint32_t* points, const uint32_t* scalars, uint32_t* out,
+                                 cudaStream_t st);
+cudaError_t msm_points_dev_bls12_381(uint32_t num, uint64_t cap, const uint64_t* offsets, int c,
+                                     const uint32_t* points, const uint32_t* scalars, uint32_t* out,
+                                     cudaStream_t st);
+cudaError_t msm_bases_dev_bn254(void* bases, uint32_t num, uint64_t cap, const uint64_t* sizes, int c,
+                                const uint32_t* scalars, uint32_t* out, cudaStream_t st);
+cudaError_t msm_bases_dev_bls12_381(void* bases, uint32_t num, uint64_t cap, const uint64_t* sizes, int c,
+                                    const uint32_t* scalars, uint32_t* out, cudaStream_t st);
 cudaError_t bases_precompute_bls12_381(void* bases, int c, cudaStream_t st);
 
 namespace {
@@ -77,6 +88,62 @@ void msm_set_window(int curve, int log2n, int c) {
   }
 }
 
+namespace {
+
+std::atomic<bool> g_phase_on{false};
+
+// One set of boundary events per host thread (and device), created on first use.
+struct PhaseClock {
+  int dev = -1;
+  cudaEvent_t ev[kMsmPhases + 1] = {};
+  bool marked[kMsmPhases + 1] = {};
+  ~PhaseClock() {
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+};
+thread_local PhaseClock t_clock;
+
+}  // namespace
+
+void set_phase_timing(bool on) { g_phase_on.store(on); }
+
+void phase_mark(int i, cudaStream_t st) {
+  if (!g_phase_on.load() || i < 0 || i > kMsmPhases) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return;
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  PhaseClock& pc = t_clock;
+  if (pc.dev != dev) {
+    for (auto& e : pc.ev) {
+      if (e) cudaEventDestroy(e);
+      e = nullptr;
+    }
+    pc.dev = dev;
+  }
+  if (!pc.ev[i] && cudaEventCreate(&pc.ev[i]) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  if (i == 0)
+    for (auto& m : pc.marked) m = false;
+  pc.marked[i] = cudaEventRecord(pc.ev[i], st) == cudaSuccess;
+}
+
+bool phase_times(float* ms) {
+  PhaseClock& pc = t_clock;
+  for (int i = 0; i <= kMsmPhases; ++i)
+    if (!pc.marked[i]) return false;
+  if (cudaEventSynchronize(pc.ev[kMsmPhases]) != cudaSuccess) return false;
+  for (int i = 0; i < kMsmPhases; ++i)
+    if (cudaEventElapsedTime(&ms[i], pc.ev[i], pc.ev[i + 1]) != cudaSuccess) return false;
+  return true;
+}
+
 int msm_reduce_log(int curve, uint64_t n) {
   if (n < 2) n = 2;
   std::lock_guard<std::mutex> lock(g_win_mu);
@@ -91,6 +158,28 @@ void msm_set_reduce_log(int curve, int log2n, int v) {
   } else {
     g_chunk_table[{curve, log2n}] = v;
   }
+}
+
+cudaError_t launch_msm_dev(int curve, uint32_t num, uint64_t cap, const uint64_t* offsets, int c,
+                           const uint32_t* points, const uint32_t* scalars, uint32_t* out,
+                           cudaStream_t st) {
+  if (c <= 0) c = msm_window(curve, num ? std::max<uint64_t>(cap / num, 2) : 2);
+  switch (curve) {
+    case 2: return msm_points_dev_bn254(num, cap, offsets, c, points, scalars, out, st);
+    case 3: return msm_points_dev_bls12_381(num, cap, offsets, c, points, scalars, out, st);
+  }
+  return cudaErrorNotSupported;
+}
+
+cudaError_t launch_msm_bases_dev(void* handle, uint32_t num, uint64_t cap, const uint64_t* sizes, int c,
+                                 const uint32_t* scalars, uint32_t* out, cudaStream_t st) {
+  const int curve = bases_curve(handle);
+  if (c <= 0) c = msm_window(curve, num ? std::max<uint64_t>(cap / num, 2) : 2);
+  switch (curve) {
+    case 2: return msm_bases_dev_bn254(handle, num, cap, sizes, c, scalars, out, st);
+    case 3: return msm_bases_dev_bls12_381(handle, num, cap, sizes, c, scalars, out, st);
+  }
+  return cudaErrorNotSupported;
 }
 
 cudaError_t launch_msm(int curve, uint32_t num, const uint64_t* offsets, const uint32_t* points,

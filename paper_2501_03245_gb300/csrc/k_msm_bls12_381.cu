@@ -18,8 +18,20 @@ cudaError_t msm_bases_bls12_381(void* bases, uint32_t num_vectors, const uint64_
 
 cudaError_t points_to_mont_bls12_381(const uint32_t* in, uint64_t n, uint32_t* out,
                                      cudaStream_t st) {
-  k_points_to_mont<BLS12_381><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(in, n, out);
+  k_points_to_mont<BLS12_381><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(in, n, nullptr, out);
   return cudaGetLastError();
+}
+
+cudaError_t msm_points_dev_bls12_381(uint32_t num, uint64_t cap, const uint64_t* offsets, int c,
+                                const uint32_t* points, const uint32_t* scalars, uint32_t* out,
+                                cudaStream_t st) {
+  return msm_detail::msm_points_dev<BLS12_381>(3, num, cap, offsets, c, points, scalars, out, st);
+}
+
+cudaError_t msm_bases_dev_bls12_381(void* bases, uint32_t num, uint64_t cap, const uint64_t* sizes, int c,
+                               const uint32_t* scalars, uint32_t* out, cudaStream_t st) {
+  return msm_detail::msm_bases_dev_t<BLS12_381>(static_cast<msm_detail::Bases*>(bases), num, cap, sizes, c,
+                                            scalars, out, st);
 }
 
 cudaError_t bases_precompute_bls12_381(void* bases, int c, cudaStream_t st) {

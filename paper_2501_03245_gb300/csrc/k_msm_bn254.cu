@@ -23,10 +23,22 @@ cudaError_t points_to_mont(int curve, const uint32_t* in, uint64_t n, uint32_t* 
                            cudaStream_t st) {
   const unsigned b = (unsigned)((n + 255) / 256);
   if (curve == 2) {
-    k_points_to_mont<BN254><<<b, 256, 0, st>>>(in, n, out);
+    k_points_to_mont<BN254><<<b, 256, 0, st>>>(in, n, nullptr, out);
     return cudaGetLastError();
   }
   return points_to_mont_bls12_381(in, n, out, st);
+}
+
+cudaError_t msm_points_dev_bn254(uint32_t num, uint64_t cap, const uint64_t* offsets, int c,
+                                const uint32_t* points, const uint32_t* scalars, uint32_t* out,
+                                cudaStream_t st) {
+  return msm_detail::msm_points_dev<BN254>(2, num, cap, offsets, c, points, scalars, out, st);
+}
+
+cudaError_t msm_bases_dev_bn254(void* bases, uint32_t num, uint64_t cap, const uint64_t* sizes, int c,
+                               const uint32_t* scalars, uint32_t* out, cudaStream_t st) {
+  return msm_detail::msm_bases_dev_t<BN254>(static_cast<msm_detail::Bases*>(bases), num, cap, sizes, c,
+                                            scalars, out, st);
 }
 
 cudaError_t bases_precompute_bn254(void* bases, int c, cudaStream_t st) {

@@ -163,6 +163,61 @@ cudaError_t gtable(int curve, const uint4** table, cudaStream_t st) {
   return cudaSuccess;
 }
 
+namespace {
+
+// y^2 = x^3 + a x + b in Montgomery form, canonical coordinates; (0, 0) is O.
+template <class C>
+__global__ void k_validate(const uint32_t* __restrict__ p, size_t n, uint8_t* __restrict__ ok) {
+  using F = typename C::Fp;
+  constexpr int N = F::N;
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t x[N], y[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    x[k] = p[2 * N * i + k];
+    y[k] = p[2 * N * i + N + k];
+  }
+  if (pt_is_inf<F>(x, y)) {
+    ok[i] = 1;
+    return;
+  }
+  if (!fe_lt_modulus<F>(x) || !fe_lt_modulus<F>(y)) {
+    ok[i] = 0;
+    return;
+  }
+  to_mont<F>(x, x);
+  to_mont<F>(y, y);
+  uint32_t lhs[N], rhs[N], t[N];
+  mont_sqr<F>(lhs, y);
+  mont_sqr<F>(t, x);
+  if (!C::A_ZERO) {
+    uint32_t a[N];
+    curve_a<C>(a);
+    fe_add<F>(t, t, a);
+  }
+  mont_mul<F>(rhs, t, x);
+#pragma unroll
+  for (int k = 0; k < N; ++k) t[k] = C::b(k);
+  fe_add<F>(rhs, rhs, t);
+  ok[i] = fe_eq<F>(lhs, rhs) ? 1 : 0;
+}
+
+}  // namespace
+
+cudaError_t launch_validate_points(int curve, size_t n, const uint32_t* p, uint8_t* ok, cudaStream_t st) {
+  const unsigned b = (unsigned)((n + 255) / 256);
+  switch (curve) {
+    case 0: k_validate<Secp256k1><<<b, 256, 0, st>>>(p, n, ok); break;
+    case 1: k_validate<P256><<<b, 256, 0, st>>>(p, n, ok); break;
+    case 2: k_validate<BN254><<<b, 256, 0, st>>>(p, n, ok); break;
+    case 3: k_validate<BLS12_381><<<b, 256, 0, st>>>(p, n, ok); break;
+    case 4: k_validate<SM2><<<b, 256, 0, st>>>(p, n, ok); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_point_add(int curve, size_t n, const uint32_t* p, const uint32_t* q,
                              uint32_t* out, int dbl, cudaStream_t st) {
   switch (curve) {

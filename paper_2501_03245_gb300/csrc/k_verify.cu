@@ -1,71 +1,38 @@
-// Launcher of the batched ECDSA verification kernel (secp256k1, P-256).
+// Dispatch of the batched ECDSA verification (secp256k1, P-256, SM2); the
+// kernels are instantiated in k_verify_<curve>*.cu.
+#include <atomic>
+
 #include "internal.h"
-#include "verify.cuh"
 
 namespace ecc {
 
+#define ECC_VERIFY_DECL(name)                                                                  \
+  cudaError_t verify_##name(size_t n, const uint8_t* hash, const uint8_t* r, const uint8_t* s, \
+                            const uint8_t* pub, uint8_t* ok, cudaStream_t st);
+ECC_VERIFY_DECL(secp256k1)
+ECC_VERIFY_DECL(p256)
+ECC_VERIFY_DECL(p256_c2)
+ECC_VERIFY_DECL(p256_c4)
+ECC_VERIFY_DECL(sm2)
+#undef ECC_VERIFY_DECL
+
 namespace {
-
-constexpr int kVerifyBlock = kGasThreads;
-
-template <class C>
-cudaError_t verify(size_t n, const uint8_t* hash, const uint8_t* r, const uint8_t* s,
-                   const uint8_t* pub, uint8_t* ok, cudaStream_t st, int curve) {
-  using Fp = typename C::Fp;
-  using Fn = typename C::Fn;
-  constexpr int B = kVerifyBlock;
-  const uint4* tg = nullptr;
-  cudaError_t e = gtable(curve, &tg, st);
-  if (e != cudaSuccess) return e;
-  // workspace: S, E, Rn (Fn) | TQ x,y (kQTable n each) | AQ, AG | M | D2 | U1B | status
-  const size_t fe = soa_bytes<Fp>(n);
-  const size_t bytes = 3 * fe + 2 * kQTable * fe + 4 * fe + fe + (kQDigits + 32 + 1) * n + 256;
-  Scratch ws;
-  e = ws.alloc(bytes, st);
-  if (e != cudaSuccess) return e;
-  uint4* v = ws.as<uint4>();
-  const size_t q = fe / 16;  // uint4 per SoA array of n elements
-  VerifyArgs<C> a;
-  a.n = n;
-  a.hash = reinterpret_cast<const uint32_t*>(hash);
-  a.r = reinterpret_cast<const uint32_t*>(r);
-  a.s = reinterpret_cast<const uint32_t*>(s);
-  a.pub = reinterpret_cast<const uint32_t*>(pub);
-  a.ok = ok;
-  a.S = SoA<Fn>{v + 0 * q, n};
-  a.E = SoA<Fn>{v + 1 * q, n};
-  a.Rn = SoA<Fn>{v + 2 * q, n};
-  const size_t T = kQTable;
-  a.TQ = PtSoA<Fp>{SoA<Fp>{v + 3 * q, T * n}, SoA<Fp>{v + (3 + T) * q, T * n}};
-  a.AQ = PtSoA<Fp>{SoA<Fp>{v + (3 + 2 * T) * q, n}, SoA<Fp>{v + (4 + 2 * T) * q, n}};
-  a.AG = PtSoA<Fp>{SoA<Fp>{v + (5 + 2 * T) * q, n}, SoA<Fp>{v + (6 + 2 * T) * q, n}};
-  a.M = SoA<Fp>{v + (7 + 2 * T) * q, n};
-  uint8_t* tail = reinterpret_cast<uint8_t*>(v + (8 + 2 * T) * q);
-  a.D2 = reinterpret_cast<int8_t*>(tail);
-  a.U1B = tail + kQDigits * n;
-  a.status = tail + (kQDigits + 32) * n;
-  const size_t te = 32 * 256;
-  a.TG = PtSoA<Fp>{SoA<Fp>{const_cast<uint4*>(tg), te}, SoA<Fp>{const_cast<uint4*>(tg) + soa_bytes<Fp>(te) / 16, te}};
-  size_t ctas = (size_t)device_sm_count() * kGasCtasPerSm;
-  size_t per = (n + ctas - 1) / ctas;
-  if (per < 32) per = 32;
-  ctas = (n + per - 1) / per;
-  a.per_cta = per;
-  const size_t smem = sizeof(GasSmem<Fp::N, B>);
-  e = cudaFuncSetAttribute(k_verify<C, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k_verify<C, B><<<(unsigned)ctas, B, smem, st>>>(a);
-  return cudaGetLastError();
-}
-
+std::atomic<int> g_gas_cluster{1};
 }  // namespace
+
+void set_gas_cluster(int ctas) { g_gas_cluster.store(ctas); }
 
 cudaError_t launch_verify(int curve, size_t n, const uint8_t* hash, const uint8_t* r,
                           const uint8_t* s, const uint8_t* pub, uint8_t* ok, cudaStream_t st) {
   switch (curve) {
-    case 0: return verify<Secp256k1>(n, hash, r, s, pub, ok, st, 0);
-    case 1: return verify<P256>(n, hash, r, s, pub, ok, st, 1);
-    case 4: return verify<SM2>(n, hash, r, s, pub, ok, st, 4);
+    case 0: return verify_secp256k1(n, hash, r, s, pub, ok, st);
+    case 1:
+      switch (g_gas_cluster.load()) {
+        case 2: return verify_p256_c2(n, hash, r, s, pub, ok, st);
+        case 4: return verify_p256_c4(n, hash, r, s, pub, ok, st);
+        default: return verify_p256(n, hash, r, s, pub, ok, st);
+      }
+    case 4: return verify_sm2(n, hash, r, s, pub, ok, st);
   }
   return cudaErrorNotSupported;
 }

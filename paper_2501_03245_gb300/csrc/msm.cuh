@@ -42,7 +42,6 @@ struct MsmInst {
   uint64_t pre_stride;
   uint32_t Wr;           // bucket rows (windows reduced separately)
   uint32_t red_log;      // log2 of the buckets per first-level reduction chunk
-  uint64_t digit_off;    // first rank slot: digit w of point j at digit_off + w n + j
 };
 
 // ------------------------------------------------------------------ digits
@@ -102,16 +101,101 @@ ECC_DEV int find_inst(const MsmInst* inst, int num, uint64_t g) {
   return lo;
 }
 
-// Histogram of the bucket ids.  The count a digit's atomic increment returns is
-// its rank inside its bucket; the rank is kept (digit w of point j of an
-// instance at digit_off + w n + j, so a warp's writes of one window are
-// contiguous) and the scatter places the digit at off[b] + rank with no atomics
-// of its own.
+// A ragged batch whose instance sizes live in device memory: the scalar rows
+// of all instances (rows [0, total)) and whether the sizes were refused.
+struct MsmDevHdr {
+  uint64_t total;
+  uint32_t failed;
+  uint32_t pad;
+};
+
+// Rows of the batch: the host's count, or the device header's when present.
+ECC_DEV uint64_t batch_rows(uint64_t host_total, const MsmDevHdr* hdr) {
+  return hdr ? hdr->total : host_total;
+}
+
+// Instance table of a ragged batch whose sizes are in device memory.  Every
+// instance has the window width, bucket rows and reduction chunk of `proto`, so
+// instance i's buckets start at i Wr 2^(c-1) and nothing else about the launch
+// sequence depends on the sizes.  rows: sizes[num] (resident bases, scalar rows
+// back to back, each size at most n_bases) or offsets[num + 1] (offsets[0] = 0,
+// point and scalar rows of instance i from offsets[i]).  Sizes that break these
+// rules or a total above `cap` leave an empty batch (total 0, failed = 1: every
+// output is O) and record ECC_EINVAL (-1) in the status word.  One CTA.
+static __global__ void k_msm_inst_dev(const uint64_t* __restrict__ rows, uint32_t num, int sizes_mode,
+                               uint64_t n_bases, uint64_t cap, MsmInst proto, MsmInst* __restrict__ inst,
+                               MsmDevHdr* hdr, int* status) {
+  __shared__ uint64_t warp_sum[32];
+  __shared__ uint64_t carry;
+  __shared__ int bad;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) {
+    carry = 0;
+    bad = !sizes_mode && rows[0] != 0;
+  }
+  __syncthreads();
+  const uint64_t per_bucket_row = (uint64_t)proto.Wr << (proto.c - 1);
+  for (uint32_t base = 0; base < num; base += blockDim.x) {
+    const uint32_t i = base + threadIdx.x;
+    uint64_t n = 0, off = 0;
+    if (i < num) {
+      if (sizes_mode) {
+        n = rows[i];
+        if (n > n_bases) bad = 1;
+      } else {
+        off = rows[i];
+        const uint64_t hi = rows[i + 1];
+        if (hi < off) bad = 1;
+        n = hi >= off ? hi - off : 0;
+      }
+    }
+    // block-wide exclusive prefix of n (scalar rows before instance i)
+    uint64_t x = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      uint64_t w = lane < nw ? warp_sum[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      if (lane < nw) warp_sum[lane] = w;
+    }
+    __syncthreads();
+    const uint64_t before = carry + (warp > 0 ? warp_sum[warp - 1] : 0) + x - n;
+    if (i < num) {
+      MsmInst m = proto;
+      m.n = (uint32_t)n;
+      m.bucket_base = (uint32_t)(i * per_bucket_row);
+      m.scalar_off = sizes_mode ? before : off;
+      m.point_off = sizes_mode ? 0 : off;
+      inst[i] = m;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) carry += warp_sum[nw - 1];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const uint64_t total = sizes_mode ? carry : rows[num];
+    const bool fail = bad || total > cap;
+    hdr->total = fail ? 0 : total;
+    hdr->failed = fail ? 1u : 0u;
+    if (fail) atomicCAS(status, 0, -1);
+  }
+}
+
+// Histogram of the bucket ids (fire-and-forget atomic increments).
 template <class C>
 __global__ void k_msm_count(const MsmInst* inst, int num, const uint32_t* __restrict__ scalars,
-                            uint64_t total, uint32_t* __restrict__ count, uint32_t* __restrict__ rank) {
+                            uint64_t total, const MsmDevHdr* hdr, uint32_t* __restrict__ count) {
   const uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  if (g >= total) return;
+  if (g >= batch_rows(total, hdr)) return;
   const MsmInst in = inst[find_inst(inst, num, g)];
   uint32_t k[8];
 #pragma unroll
@@ -119,10 +203,9 @@ __global__ void k_msm_count(const MsmInst* inst, int num, const uint32_t* __rest
   scalar_mod_r<C>(k);
   const uint32_t half = 1u << (in.c - 1);
   const uint32_t row = in.pre_stride ? 0u : half;
-  const uint64_t slot = in.digit_off + (g - in.scalar_off);
   for_each_digit(k, in.c, in.W, [&](int w, int d) {
     const uint32_t b = in.bucket_base + w * row + (uint32_t)(d < 0 ? -d : d) - 1;
-    rank[slot + (uint64_t)w * in.n] = atomicAdd(count + b, 1u);
+    atomicAdd(count + b, 1u);
   });
 }
 
@@ -132,11 +215,11 @@ __global__ void k_msm_count(const MsmInst* inst, int num, const uint32_t* __rest
 // per-chunk bucket cursor starts there).
 template <class C>
 __global__ void k_msm_scatter(const MsmInst* inst, int num, const uint32_t* __restrict__ scalars,
-                              uint64_t total, const uint32_t* __restrict__ off,
-                              const uint32_t* __restrict__ rank, uint32_t* __restrict__ vals,
-                              uint64_t n_chunks, uint32_t* __restrict__ cur) {
+                              uint64_t total, const MsmDevHdr* hdr, uint32_t* __restrict__ cursor,
+                              uint32_t* __restrict__ vals, uint64_t n_chunks,
+                              uint32_t* __restrict__ cur) {
   const uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  if (g >= total) return;
+  if (g >= batch_rows(total, hdr)) return;
   const MsmInst in = inst[find_inst(inst, num, g)];
   uint32_t k[8];
 #pragma unroll
@@ -145,10 +228,9 @@ __global__ void k_msm_scatter(const MsmInst* inst, int num, const uint32_t* __re
   const uint32_t half = 1u << (in.c - 1);
   const uint32_t row = in.pre_stride ? 0u : half;
   const uint64_t pidx = in.point_off + (g - in.scalar_off);
-  const uint64_t slot = in.digit_off + (g - in.scalar_off);
   for_each_digit(k, in.c, in.W, [&](int w, int d) {
     const uint32_t b = in.bucket_base + w * row + (uint32_t)(d < 0 ? -d : d) - 1;
-    const uint32_t p = off[b] + rank[slot + (uint64_t)w * in.n];
+    const uint32_t p = atomicAdd(cursor + b, 1u);
     const uint32_t idx = (uint32_t)(pidx + (uint64_t)w * in.pre_stride);  // < 2^31 (host check)
     vals[(uint64_t)(p % kAccChunk) * n_chunks + p / kAccChunk] = idx | (d < 0 ? 0x80000000u : 0u);
     if (p % kAccChunk == 0) cur[p / kAccChunk] = b;
@@ -179,7 +261,6 @@ struct AccArgs {
   PtSoA<F> S;             // running sum per chunk
   PtSoA<F> partial;       // partial bucket sums
   SoA<F> M;               // GAS prefix products
-  uint64_t per_cta;
 };
 
 template <class C>
@@ -487,8 +568,11 @@ __global__ void __launch_bounds__(BLOCK, kGasResidentThreads / BLOCK) k_msm_accu
   auto& sm = gas_smem<N, BLOCK>();
   const uint32_t entries = a.off[a.n_buckets];
   const uint64_t used = (entries + kAccChunk - 1) / kAccChunk;
-  const uint64_t begin = blockIdx.x * a.per_cta;
-  uint64_t end = begin + a.per_cta;
+  // equal shares of the chunks actually used (at least 32 per CTA)
+  uint64_t per = (used + gridDim.x - 1) / gridDim.x;
+  if (per < 32) per = 32;
+  const uint64_t begin = blockIdx.x * per;
+  uint64_t end = begin + per;
   if (end > used) end = used;
   if (end < begin) end = begin;
   for (int j = 0; j < kAccChunk; ++j) acc_round_staged<C, BLOCK>(a, j, entries, begin, end, sm);
@@ -561,27 +645,7 @@ ECC_DEV uint32_t lower_bound_u32(const uint32_t* v, uint32_t n, uint64_t x) {
 }
 
 // Round with stride h: slot l of a bucket with k partials adds slot l + h for
-// every l that is a multiple of 2h with l + h < k.
-template <class C>
-struct FoldOp {
-  using F = typename C::Fp;
-  static constexpr int N = F::N;
-  const FoldArgs<C>* a;
-  uint32_t h;
-  ECC_DEV int den(uint64_t s, uint32_t* d) const {
-    uint32_t x0[N], y0[N], x1[N], y1[N];
-    a->partial.load(s, x0, y0);
-    a->partial.load(s + h, x1, y1);
-    return add_den<C>(d, x0, y0, x1, y1);
-  }
-  ECC_DEV void finish(uint64_t s, int kind, const uint32_t* inv) const {
-    uint32_t x0[N], y0[N], x1[N], y1[N];
-    a->partial.load(s, x0, y0);
-    a->partial.load(s + h, x1, y1);
-    add_finish<C>(x0, y0, kind, inv, x0, y0, x1, y1);
-    a->partial.store(s, x0, y0);
-  }
-};
+// every l that is a multiple of 2h with l + h < k (fold_round_staged below).
 
 // Exclusive prefix sum of v over the CTA (warp shuffles, then the warp
 // totals); total gets the CTA sum.  wsum: BLOCK / 32 shared words.
@@ -611,6 +675,133 @@ ECC_DEV uint32_t cta_exclusive_sum(uint32_t v, uint32_t* wsum, uint32_t& total) 
   total = wsum[NW - 1];
   __syncthreads();  // wsum is reused
   return before + x - v;
+}
+
+// One fold round over the listed additions (slot s += slot s + h) with the
+// operands staged in shared memory: the two partial sums and the prefix
+// product of each addition (5 G 16-byte vectors, G = N / 4), the thread's own
+// column of the GAS tree (dead outside cta_invert).  The slot list is read two
+// additions ahead and the copies run one addition ahead.  With 8 limbs DCWPA
+// holds every operand in registers from the top of an addition, so the next
+// copies start at once; with 12 limbs it forms the two DCWPA products first
+// and starts the next copies once the finish operands are in registers.
+template <class C, int BLOCK>
+__device__ void fold_round_staged(const FoldArgs<C>& a, uint32_t h, uint64_t s0, uint32_t n_ops,
+                                  GasSmem<C::Fp::N, BLOCK>& sm) {
+  using F = typename C::Fp;
+  constexpr int N = F::N;
+  constexpr int G = N / 4;
+  constexpr int X0 = 0, Y0 = G, X1 = 2 * G, Y1 = 3 * G, PRE = 4 * G;
+  constexpr bool kEarly = N <= 8;
+  static_assert(sizeof(sm.tree) >= 5 * G * BLOCK * sizeof(uint4), "staging fits the GAS tree");
+  uint4* const base = &sm.tree[0][0][0] + threadIdx.x;
+  auto at = [&](int k) { return base + k * BLOCK; };
+  auto get = [&](int k0, uint32_t* r) {
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const uint4 q = *at(k0 + g);
+      r[4 * g] = q.x;
+      r[4 * g + 1] = q.y;
+      r[4 * g + 2] = q.z;
+      r[4 * g + 3] = q.w;
+    }
+  };
+  auto stage = [&](uint32_t sl, bool full) {
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      ptx::cp_async16(at(X0 + g), a.partial.x.vec + g * a.partial.x.stride + sl);
+      ptx::cp_async16(at(Y0 + g), a.partial.y.vec + g * a.partial.y.stride + sl);
+      ptx::cp_async16(at(X1 + g), a.partial.x.vec + g * a.partial.x.stride + sl + h);
+      ptx::cp_async16(at(Y1 + g), a.partial.y.vec + g * a.partial.y.stride + sl + h);
+      if (full) ptx::cp_async16(at(PRE + g), a.M.vec + g * a.M.stride + sl);
+    }
+    ptx::cp_async_commit();
+  };
+  const uint32_t t = threadIdx.x;
+  // ---- compress, ascending
+  uint32_t run[N];
+  fe_set_one<F>(run);
+  uint32_t sA = 0, sB = 0;
+  if (t < n_ops) {
+    sA = a.ops[s0 + t];
+    stage(sA, false);
+    if (t + BLOCK < n_ops) sB = a.ops[s0 + t + BLOCK];
+  }
+  for (uint32_t e = t; e < n_ops; e += BLOCK) {
+    ptx::cp_async_wait_all();
+    uint32_t x0[N], y0[N], x1[N], y1[N], d[N];
+    get(X0, x0);
+    get(Y0, y0);
+    get(X1, x1);
+    get(Y1, y1);
+    uint32_t sC = 0;
+    if (e + BLOCK < n_ops) {
+      stage(sB, false);
+      if (e + 2 * BLOCK < n_ops) sC = a.ops[s0 + e + 2 * BLOCK];
+    }
+    a.M.store(sA, run);
+    add_den<C>(d, x0, y0, x1, y1);
+    mont_mul<F>(run, run, d);
+    sA = sB;
+    sB = sC;
+  }
+  // ---- inverse of the CTA's product (GAS, Section 3.2)
+  uint32_t inv[N];
+  cta_invert<F, BLOCK>(inv, run, sm);
+  if (t >= n_ops) return;
+  // ---- DCWPA, descending
+  const uint32_t last = t + ((n_ops - 1 - t) / BLOCK) * BLOCK;
+  sA = a.ops[s0 + last];
+  stage(sA, true);
+  sB = last >= t + BLOCK ? a.ops[s0 + last - BLOCK] : 0u;
+  for (uint32_t e = last;; e -= BLOCK) {
+    ptx::cp_async_wait_all();
+    const bool more = e >= t + BLOCK;
+    uint32_t sC = 0;
+    auto ahead = [&]() {
+      if (!more) return;
+      stage(sB, true);
+      if (e >= t + 2 * BLOCK) sC = a.ops[s0 + e - 2 * BLOCK];
+    };
+    uint32_t x0[N], y0[N], x1[N], y1[N], d[N], mine[N];
+    int kind;
+    if constexpr (kEarly) {
+      uint32_t pre[N];
+      get(X0, x0);
+      get(Y0, y0);
+      get(X1, x1);
+      get(Y1, y1);
+      get(PRE, pre);
+      ahead();
+      kind = add_den<C>(d, x0, y0, x1, y1);
+      mont_mul<F>(mine, inv, pre);
+    } else {
+      get(X0, x0);
+      get(X1, x1);
+      if (fe_is_zero<F>(x0) || fe_is_zero<F>(x1) || fe_eq<F>(x0, x1)) {
+        get(Y0, y0);
+        get(Y1, y1);
+        kind = add_den<C>(d, x0, y0, x1, y1);
+      } else {
+        kind = ADD_REGULAR;
+        fe_sub<F>(d, x1, x0);
+      }
+      {
+        uint32_t pre[N];
+        get(PRE, pre);
+        mont_mul<F>(mine, inv, pre);
+      }
+      get(Y0, y0);
+      get(Y1, y1);
+      ahead();
+    }
+    mont_mul<F>(inv, inv, d);
+    add_finish<C>(x0, y0, kind, mine, x0, y0, x1, y1);
+    a.partial.store(sA, x0, y0);
+    if (!more) break;
+    sA = sB;
+    sB = sC;
+  }
 }
 
 // Each round first lists the CTA's pair additions (slot of the left operand)
@@ -654,31 +845,7 @@ __global__ void __launch_bounds__(BLOCK, kGasResidentThreads / BLOCK) k_msm_fold
       for (uint32_t l = 0; l + h < k; l += 2 * h) a.ops[s0 + pos++] = p + l;
     }
     __syncthreads();  // the list is complete
-    FoldOp<C> op{&a, h};
-    uint32_t run[N];
-    fe_set_one<F>(run);
-    for (uint32_t e = threadIdx.x; e < n_ops; e += BLOCK) {
-      const uint32_t s = a.ops[s0 + e];
-      uint32_t d[N];
-      a.M.store(s, run);
-      op.den(s, d);
-      mont_mul<F>(run, run, d);
-    }
-    uint32_t inv[N];
-    cta_invert<F, BLOCK>(inv, run, sm);
-    if (threadIdx.x < n_ops) {
-      const uint32_t last = threadIdx.x + ((n_ops - 1 - threadIdx.x) / BLOCK) * BLOCK;
-      for (uint32_t e = last + BLOCK; e > threadIdx.x;) {
-        e -= BLOCK;
-        const uint32_t s = a.ops[s0 + e];
-        uint32_t d[N], pre[N], mine[N];
-        const int kind = op.den(s, d);
-        a.M.load(s, pre);
-        mont_mul<F>(mine, inv, pre);
-        mont_mul<F>(inv, inv, d);
-        op.finish(s, kind, mine);
-      }
-    }
+    fold_round_staged<C, BLOCK>(a, h, s0, n_ops, sm);
   }
 }
 
@@ -800,6 +967,220 @@ struct AffRedRound {
   }
 };
 
+// ---- 8-limb fields: the walk's rounds with their operands staged in shared
+// memory.  Each thread owns two sets (a double buffer) of 6 G 16-byte vectors
+// holding S, R and the bucket's partial sum P (x and y of each, G = N / 4
+// vectors per element, layout [vector][thread]): one set holds the current
+// item's operands while the cp.async copies of the next item's land in the
+// other.  The thread's own column of the GAS tree (dead outside cta_invert)
+// provides 5 G of the vectors; the rest follows the GasSmem block.  The
+// item's cursor words are loaded two items ahead, its bucket offsets (the
+// event step) one item ahead together with the copies, and DCWPA's prefix
+// product one item ahead into registers.
+template <int N, int BLOCK>
+struct RedStage {
+  static constexpr int G = N / 4;
+  static constexpr int SX = 0, SY = G, RX = 2 * G, RY = 3 * G, PX = 4 * G, PY = 5 * G;
+  static constexpr int SET = 6 * G;
+  static constexpr int TREE = 5 * G;
+  static constexpr int EXTRA = 2 * SET - TREE;
+  uint4* tree;
+  uint4* extra;
+  ECC_DEV uint4* at(int set, int k) const {
+    const int s = set * SET + k;
+    return (s < TREE ? tree + s * BLOCK : extra + (s - TREE) * BLOCK) + threadIdx.x;
+  }
+  ECC_DEV void get(int set, int k0, uint32_t* r) const {
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const uint4 p = *at(set, k0 + g);
+      r[4 * g] = p.x;
+      r[4 * g + 1] = p.y;
+      r[4 * g + 2] = p.z;
+      r[4 * g + 3] = p.w;
+    }
+  }
+};
+
+template <int N, int BLOCK>
+constexpr size_t red_smem_bytes() {
+  return sizeof(GasSmem<N, BLOCK>) + (size_t)RedStage<N, BLOCK>::EXTRA * BLOCK * sizeof(uint4);
+}
+
+// Copies item t's S and R, and the partial sum its A event adds.
+template <class C, int BLOCK>
+ECC_DEV void red_stage(const RedStage<C::Fp::N, BLOCK>& sg, int set, const AffRedArgs<C>& a,
+                       uint64_t t, const RedStep& st) {
+  using S = RedStage<C::Fp::N, BLOCK>;
+#pragma unroll
+  for (int g = 0; g < S::G; ++g) {
+    ptx::cp_async16(sg.at(set, S::SX + g), a.S.x.vec + g * a.S.x.stride + t);
+    ptx::cp_async16(sg.at(set, S::SY + g), a.S.y.vec + g * a.S.y.stride + t);
+    ptx::cp_async16(sg.at(set, S::RX + g), a.R.x.vec + g * a.R.x.stride + t);
+    ptx::cp_async16(sg.at(set, S::RY + g), a.R.y.vec + g * a.R.y.stride + t);
+  }
+  if (st.opA) {
+#pragma unroll
+    for (int g = 0; g < S::G; ++g) {
+      ptx::cp_async16(sg.at(set, S::PX + g), a.partial.x.vec + g * a.partial.x.stride + st.slot);
+      ptx::cp_async16(sg.at(set, S::PY + g), a.partial.y.vec + g * a.partial.y.stride + st.slot);
+    }
+  }
+  ptx::cp_async_commit();
+}
+
+// One round of the walk over the items [begin, end) of this CTA; returns
+// whether any of this thread's items has events left.
+template <class C, int BLOCK>
+__device__ bool red_round_staged(const AffRedArgs<C>& a, uint64_t begin, uint64_t end,
+                                 GasSmem<C::Fp::N, BLOCK>& sm, uint4* extra) {
+  using F = typename C::Fp;
+  constexpr int N = F::N;
+  using S = RedStage<N, BLOCK>;
+  const S sg{&sm.tree[0][0][0], extra};
+  const uint64_t i0 = begin + threadIdx.x;
+  bool more = false;
+  // cursor words of item t: (ep, ad, lo)
+  uint32_t e1 = 0, a1 = 0, l1 = 0;
+  auto cursor = [&](uint64_t t, uint32_t& e, uint32_t& d, uint32_t& l) {
+    e = a.cur_e[t];
+    d = a.cur_a[t];
+    l = a.lo_b[t];
+  };
+  // ---- compress, ascending
+  uint32_t run[N];
+  fe_set_one<F>(run);
+  RedStep st0{};
+  if (i0 < end) {
+    uint32_t e0, d0, l0;
+    cursor(i0, e0, d0, l0);
+    st0 = red_step(a.poff, e0, d0, l0);
+    red_stage<C, BLOCK>(sg, 0, a, i0, st0);
+    if (i0 + BLOCK < end) cursor(i0 + BLOCK, e1, a1, l1);
+  }
+  int set = 0;
+  for (uint64_t t = i0; t < end; t += BLOCK, set ^= 1) {
+    RedStep st1{};
+    const bool next = t + BLOCK < end;
+    if (next) {
+      st1 = red_step(a.poff, e1, a1, l1);
+      red_stage<C, BLOCK>(sg, set ^ 1, a, t + BLOCK, st1);
+      if (t + 2 * BLOCK < end) cursor(t + 2 * BLOCK, e1, a1, l1);
+      ptx::cp_async_wait_prior();
+    } else {
+      ptx::cp_async_wait_all();
+    }
+    a.M.store(t, run);
+    uint32_t d[N];
+    if (st0.opS) {
+      uint32_t xs[N], ys[N], xr[N], yr[N];
+      sg.get(set, S::SX, xs);
+      sg.get(set, S::SY, ys);
+      sg.get(set, S::RX, xr);
+      sg.get(set, S::RY, yr);
+      add_den<C>(d, xs, ys, xr, yr);
+      mont_mul<F>(run, run, d);
+    }
+    if (st0.opA) {
+      uint32_t xr[N], yr[N], xp[N], yp[N];
+      sg.get(set, S::RX, xr);
+      sg.get(set, S::RY, yr);
+      sg.get(set, S::PX, xp);
+      sg.get(set, S::PY, yp);
+      add_den<C>(d, xr, yr, xp, yp);
+      mont_mul<F>(run, run, d);
+    }
+    st0 = st1;
+  }
+  // ---- inverse of the CTA's product (GAS, Section 3.2); every copy of this
+  // thread has landed (waited above), so its tree column is free
+  uint32_t inv[N];
+  cta_invert<F, BLOCK>(inv, run, sm);
+  if (i0 >= end) return false;
+  // ---- DCWPA, descending
+  const uint64_t last = i0 + ((end - 1 - i0) / BLOCK) * BLOCK;
+  uint32_t e0, d0, lo0;
+  cursor(last, e0, d0, lo0);
+  st0 = red_step(a.poff, e0, d0, lo0);
+  red_stage<C, BLOCK>(sg, 0, a, last, st0);
+  uint32_t pre0[N];
+  a.M.load(last, pre0);
+  if (last >= i0 + BLOCK) cursor(last - BLOCK, e1, a1, l1);
+  set = 0;
+  for (uint64_t t = last;; t -= BLOCK, set ^= 1) {
+    const bool next = t >= i0 + BLOCK;
+    RedStep st1{};
+    uint32_t pre1n[N], lo1 = 0;
+    if (next) {
+      st1 = red_step(a.poff, e1, a1, l1);
+      lo1 = l1;
+      red_stage<C, BLOCK>(sg, set ^ 1, a, t - BLOCK, st1);
+      a.M.load(t - BLOCK, pre1n);
+      if (t >= i0 + 2 * BLOCK) cursor(t - 2 * BLOCK, e1, a1, l1);
+      ptx::cp_async_wait_prior();
+    } else {
+      ptx::cp_async_wait_all();
+    }
+    // the item's two denominators again (recompute), then its two inverses
+    uint32_t dS[N], dA[N];
+    int kind_s = ADD_RET_T, kind_a = ADD_RET_T;
+    fe_set_one<F>(dS);
+    fe_set_one<F>(dA);
+    if (st0.opS) {
+      uint32_t xs[N], ys[N], xr[N], yr[N];
+      sg.get(set, S::SX, xs);
+      sg.get(set, S::SY, ys);
+      sg.get(set, S::RX, xr);
+      sg.get(set, S::RY, yr);
+      kind_s = add_den<C>(dS, xs, ys, xr, yr);
+    }
+    if (st0.opA) {
+      uint32_t xr[N], yr[N], xp[N], yp[N];
+      sg.get(set, S::RX, xr);
+      sg.get(set, S::RY, yr);
+      sg.get(set, S::PX, xp);
+      sg.get(set, S::PY, yp);
+      kind_a = add_den<C>(dA, xr, yr, xp, yp);
+    }
+    uint32_t invS[N], invA[N];
+    {
+      uint32_t pre1[N];
+      mont_mul<F>(pre1, pre0, dS);
+      mont_mul<F>(invA, inv, pre1);
+    }
+    mont_mul<F>(inv, inv, dA);
+    mont_mul<F>(invS, inv, pre0);
+    mont_mul<F>(inv, inv, dS);
+    if (st0.opS || st0.opA) {
+      uint32_t xr[N], yr[N];
+      sg.get(set, S::RX, xr);
+      sg.get(set, S::RY, yr);
+      if (st0.opS) {  // S += R, with R of before this round's A event
+        uint32_t xs[N], ys[N];
+        sg.get(set, S::SX, xs);
+        sg.get(set, S::SY, ys);
+        add_finish<C>(xs, ys, kind_s, invS, xs, ys, xr, yr);
+        a.S.store(t, xs, ys);
+      }
+      if (st0.opA) {  // R += the bucket's sum
+        uint32_t xp[N], yp[N];
+        sg.get(set, S::PX, xp);
+        sg.get(set, S::PY, yp);
+        add_finish<C>(xr, yr, kind_a, invA, xr, yr, xp, yp);
+        a.R.store(t, xr, yr);
+      }
+      a.cur_e[t] = st0.ep2;
+      a.cur_a[t] = st0.ad2;
+      more |= st0.ep2 != lo0;
+    }
+    if (!next) break;
+    st0 = st1;
+    lo0 = lo1;
+    fe_copy<F>(pre0, pre1n);
+  }
+  return more;
+}
+
 // R <- 2 R for every item whose chunk needs more than k doublings (batched PDBL)
 template <class C>
 struct AffDblRound {
@@ -863,10 +1244,16 @@ __global__ void __launch_bounds__(BLOCK, kGasResidentThreads / BLOCK)
   // one bounded loop: each round completes at least one event of every live
   // item, and an item has at most 2^(rlog + 1) events
   while (__syncthreads_or(more)) {
-    AffRedRound<C> rd{&a};
-    rd.more = false;
-    batch_round<F, BLOCK>(rd, begin, end, a.M, sm);
-    more = rd.more;
+    if constexpr (N == 8) {
+      extern __shared__ __align__(16) unsigned char ecc_dyn_smem[];
+      uint4* extra = reinterpret_cast<uint4*>(ecc_dyn_smem + sizeof(GasSmem<N, BLOCK>));
+      more = red_round_staged<C, BLOCK>(a, begin, end, sm, extra);
+    } else {
+      AffRedRound<C> rd{&a};
+      rd.more = false;
+      batch_round<F, BLOCK>(rd, begin, end, a.M, sm);
+      more = rd.more;
+    }
   }
   // R <- 2^rlog R: as many doubling rounds as the CTA's largest chunk needs
   for (uint32_t k = 0; k < (uint32_t)kRedLog1Max; ++k) {
@@ -943,14 +1330,23 @@ __global__ void k_msm_reduce_level(const LevelSeg* segs, uint32_t n_segs, uint64
 }
 
 // result_i = sum_w 2^(c w) S_w (Horner), converted to canonical affine limbs;
-// instance i's window sums are S[fin[i] + w].
+// instance i's window sums are S[fin[i] + w].  Thread t takes instance
+// order[t]: the host lists the instances grouped by window width, so the lanes
+// of a warp run chains of one length (a warp executes the longest chain among
+// its lanes).
 template <class C>
-__global__ void k_msm_combine(const MsmInst* inst, const uint64_t* fin, uint32_t num,
-                              const Jac<typename C::Fp>* S, uint32_t* out_all) {
+__global__ void k_msm_combine(const MsmInst* inst, const uint64_t* fin, const uint32_t* order,
+                              uint32_t num, const Jac<typename C::Fp>* S, const MsmDevHdr* hdr,
+                              uint32_t* out_all) {
   using F = typename C::Fp;
   constexpr int N = F::N;
-  const uint32_t id = blockIdx.x * blockDim.x + threadIdx.x;
-  if (id >= num) return;
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= num) return;
+  const uint32_t id = order[t];
+  if (hdr && hdr->failed) {  // refused sizes: O, written (0, 0)
+    for (int q = 0; q < 2 * N; ++q) out_all[(uint64_t)id * 2 * N + q] = 0;
+    return;
+  }
   const uint32_t c = inst[id].c, W = inst[id].Wr;
   const Jac<F>* Sw = S + fin[id];
   Jac<F> acc = Sw[W - 1];
@@ -972,11 +1368,12 @@ __global__ void k_msm_combine(const MsmInst* inst, const uint64_t* fin, uint32_t
 
 // canonical AoS points -> Montgomery AoS points (gather layout of the bases)
 template <class C>
-__global__ void k_points_to_mont(const uint32_t* __restrict__ in, uint64_t n, uint32_t* __restrict__ out) {
+__global__ void k_points_to_mont(const uint32_t* __restrict__ in, uint64_t n, const MsmDevHdr* hdr,
+                                 uint32_t* __restrict__ out) {
   using F = typename C::Fp;
   constexpr int N = F::N;
   const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if (i >= batch_rows(n, hdr)) return;
   uint32_t x[N], y[N];
 #pragma unroll
   for (int q = 0; q < N; ++q) {

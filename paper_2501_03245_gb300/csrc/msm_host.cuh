@@ -38,9 +38,22 @@ struct Layout {
   uint64_t buckets = 0, entries_max = 0, n_chunks = 0, total_points = 0;
 };
 
+// Instance sizes held in device memory (capture-time capacity): rows are
+// sizes[num] (sizes_mode, resident bases) or offsets[num + 1]; every instance
+// has the layout of L.inst[0], and L's totals are the capacity.
+struct DevRows {
+  const uint64_t* rows;
+  int sizes_mode;
+  uint64_t n_bases;
+  uint64_t cap;
+};
+
+// raw_points (optional): canonical caller points to convert into the gather
+// layout first (rows [0, total) of the batch); otherwise bases_mont is used.
 template <class C>
 cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, const uint32_t* scalars,
-                    uint32_t* out, cudaStream_t st) {
+                    uint32_t* out, cudaStream_t st, const DevRows* dev = nullptr,
+                    const uint32_t* raw_points = nullptr) {
   using F = typename C::Fp;
   constexpr int N = F::N;
   const int num = (int)L.inst.size();
@@ -51,22 +64,25 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
   const uint64_t sz_inst = up(num * sizeof(MsmInst));
   const uint64_t sz_b1 = up((B + 1) * 4);
   const uint64_t sz_kv = up(kAccChunk * NC * 4), sz_cur = up(NC * 4);
-  const uint64_t sz_rank = up(std::max<uint64_t>(L.entries_max, 1) * 4);
   const uint64_t sz_S = soa_bytes<F>(NC), sz_P = soa_bytes<F>(n_part);
   const uint64_t sz_ops = up(n_part * 4);
   // per chunk: running sum (x, y) and prefix product
   constexpr uint64_t kChunkArrays = 3;
-  const uint64_t bytes =
-      sz_inst + 4 * sz_b1 + sz_kv + sz_cur + sz_rank + kChunkArrays * sz_S + 3 * sz_P + sz_ops + 256;
+  const uint64_t sz_hdr = up(sizeof(MsmDevHdr));
+  const uint64_t sz_pts = raw_points ? up(std::max<uint64_t>(L.total_points, 1) * 2 * N * 4) : 0;
+  const uint64_t bytes = sz_inst + sz_hdr + sz_pts + 5 * sz_b1 + sz_kv + sz_cur + kChunkArrays * sz_S +
+                         3 * sz_P + sz_ops + 256;
   Scratch ws;
   cudaError_t e = ws.alloc(bytes, st);
   if (e != cudaSuccess) return e;
   char* p = ws.as<char>();
   auto take = [&](uint64_t b) { char* r = p; p += b; return r; };
   MsmInst* d_inst = reinterpret_cast<MsmInst*>(take(sz_inst));
+  MsmDevHdr* hdr = dev ? reinterpret_cast<MsmDevHdr*>(take(sz_hdr)) : nullptr;
+  uint32_t* pts_mont = raw_points ? reinterpret_cast<uint32_t*>(take(sz_pts)) : nullptr;
   uint32_t* count = reinterpret_cast<uint32_t*>(take(sz_b1));
   uint32_t* off = reinterpret_cast<uint32_t*>(take(sz_b1));
-  uint32_t* rank = reinterpret_cast<uint32_t*>(take(sz_rank));
+  uint32_t* cursor = reinterpret_cast<uint32_t*>(take(sz_b1));
   uint32_t* npart = reinterpret_cast<uint32_t*>(take(sz_b1));
   uint32_t* poff = reinterpret_cast<uint32_t*>(take(sz_b1));
   uint32_t* vals = reinterpret_cast<uint32_t*>(take(sz_kv));
@@ -74,22 +90,37 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
   uint4* sbuf = reinterpret_cast<uint4*>(take(kChunkArrays * sz_S));
   uint4* pbuf = reinterpret_cast<uint4*>(take(3 * sz_P));
   uint32_t* fold_ops = reinterpret_cast<uint32_t*>(take(sz_ops));
-  e = upload_words(d_inst, L.inst.data(), num * sizeof(MsmInst), st);
+  if (dev) {
+    k_msm_inst_dev<<<1, 1024, 0, st>>>(dev->rows, (uint32_t)num, dev->sizes_mode, dev->n_bases, dev->cap,
+                                       L.inst[0], d_inst, hdr, status_word());
+    e = cudaGetLastError();
+  } else {
+    e = upload_words(d_inst, L.inst.data(), num * sizeof(MsmInst), st);
+  }
   if (e != cudaSuccess) return e;
+  if (raw_points && L.total_points) {
+    k_points_to_mont<C><<<(unsigned)((L.total_points + 255) / 256), 256, 0, st>>>(raw_points, L.total_points,
+                                                                                 hdr, pts_mont);
+    bases_mont = pts_mont;
+  }
+  phase_mark(0, st);
   // ---- 1-2: digits, counting sort by bucket id
   e = cudaMemsetAsync(count, 0, (B + 1) * 4, st);
   if (e != cudaSuccess) return e;
   const unsigned pb = (unsigned)((L.total_points + 255) / 256);
   if (L.total_points)
-    k_msm_count<C><<<pb, 256, 0, st>>>(d_inst, num, scalars, L.total_points, count, rank);
+    k_msm_count<C><<<pb, 256, 0, st>>>(d_inst, num, scalars, L.total_points, hdr, count);
   e = exclusive_scan(count, B, off, st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(cursor, off, B * 4, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return e;
   if (B) k_msm_npart<<<(unsigned)((B + 255) / 256), 256, 0, st>>>(off, (uint32_t)B, npart);
   e = exclusive_scan(npart, B, poff, st);
   if (e != cudaSuccess) return e;
   if (L.total_points)
-    k_msm_scatter<C><<<pb, 256, 0, st>>>(d_inst, num, scalars, L.total_points, off, rank, vals, NC,
+    k_msm_scatter<C><<<pb, 256, 0, st>>>(d_inst, num, scalars, L.total_points, hdr, cursor, vals, NC,
                                           cur);
+  phase_mark(1, st);
   // ---- 3: bucket accumulation (batched affine, one launch)
   AccArgs<C> a;
   a.vals = vals;
@@ -102,11 +133,9 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
   a.S = PtSoA<F>{SoA<F>{sbuf, NC}, SoA<F>{sbuf + sz_S / 16, NC}};
   a.M = SoA<F>{sbuf + 2 * sz_S / 16, NC};
   a.partial = PtSoA<F>{SoA<F>{pbuf, n_part}, SoA<F>{pbuf + sz_P / 16, n_part}};
+  // persistent CTAs; each takes an equal share of the chunks the sort filled
   uint64_t ctas = (uint64_t)device_sm_count() * kGasCtasPerSm;
-  uint64_t per = (NC + ctas - 1) / ctas;
-  if (per < 32) per = 32;
-  ctas = (NC + per - 1) / per;
-  a.per_cta = per;
+  ctas = std::max<uint64_t>(1, std::min<uint64_t>(ctas, (NC + 31) / 32));
   const size_t smem = sizeof(GasSmem<N, kAccBlock>);
   e = cudaFuncSetAttribute(k_msm_accumulate<C, kAccBlock>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -114,6 +143,7 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
   k_msm_accumulate<C, kAccBlock><<<(unsigned)ctas, kAccBlock, smem, st>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  phase_mark(2, st);
   // ---- fold the partial sums of every bucket into its first slot
   if (B) {
     FoldArgs<C> f;
@@ -129,6 +159,7 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
+  phase_mark(3, st);
   // ---- 4: bucket reduction.  Instances are grouped by window width (same
   // level structure); the items of every level are laid out group-major so a
   // level of all groups is one launch.
@@ -187,7 +218,14 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
   }
   uint64_t seg_words = 0;
   for (size_t l = 2; l <= levels; ++l) seg_words += up(segs[l].size() * sizeof(LevelSeg));
-  const uint64_t sz_red = up(ranges.size() * sizeof(RedRange)) + up(num * 8ull) + seg_words +
+  // combination order: instances grouped by (rows, window width), so a warp's
+  // Horner chains have one length
+  std::vector<uint32_t> order(num);
+  for (int i = 0; i < num; ++i) order[i] = (uint32_t)i;
+  std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
+    return std::make_pair(L.inst[x].Wr, L.inst[x].c) < std::make_pair(L.inst[y].Wr, L.inst[y].c);
+  });
+  const uint64_t sz_red = up(ranges.size() * sizeof(RedRange)) + up(num * 8ull) + up(num * 4ull) + seg_words +
                           2 * up(jac_total * sizeof(Jac<F>)) + 4 * up(items * 4) +
                           5 * soa_bytes<F>(std::max<uint64_t>(items, 1)) + 256;
   Scratch rs;
@@ -197,6 +235,7 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
   auto take_r = [&](uint64_t b) { char* r = q; q += up(b); return r; };
   RedRange* d_ranges = reinterpret_cast<RedRange*>(take_r(ranges.size() * sizeof(RedRange)));
   uint64_t* d_fin = reinterpret_cast<uint64_t*>(take_r(num * 8ull));
+  uint32_t* d_order = reinterpret_cast<uint32_t*>(take_r(num * 4ull));
   std::vector<LevelSeg*> d_segs(levels + 1, nullptr);
   for (size_t l = 2; l <= levels; ++l) d_segs[l] = reinterpret_cast<LevelSeg*>(take_r(segs[l].size() * sizeof(LevelSeg)));
   Jac<F>* JR = reinterpret_cast<Jac<F>*>(take_r(jac_total * sizeof(Jac<F>)));
@@ -210,6 +249,8 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
   e = upload_words(d_ranges, ranges.data(), ranges.size() * sizeof(RedRange), st);
   if (e != cudaSuccess) return e;
   e = upload_words(d_fin, fin.data(), num * 8ull, st);
+  if (e != cudaSuccess) return e;
+  e = upload_words(d_order, order.data(), num * 4ull, st);
   if (e != cudaSuccess) return e;
   for (size_t l = 2; l <= levels; ++l) {
     e = upload_words(d_segs[l], segs[l].data(), segs[l].size() * sizeof(LevelSeg), st);
@@ -238,10 +279,11 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
     if (rper < 32) rper = 32;
     rctas = (items + rper - 1) / rper;
     r.per_cta = rper;
+    const size_t rsmem = N == 8 ? red_smem_bytes<N, kAccBlock>() : smem;
     e = cudaFuncSetAttribute(k_msm_reduce_affine<C, kAccBlock>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem);
     if (e != cudaSuccess) return e;
-    k_msm_reduce_affine<C, kAccBlock><<<(unsigned)rctas, kAccBlock, smem, st>>>(r);
+    k_msm_reduce_affine<C, kAccBlock><<<(unsigned)rctas, kAccBlock, rsmem, st>>>(r);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -252,12 +294,14 @@ cudaError_t run_set(int curve, const Layout& L, const uint32_t* bases_mont, cons
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
+  phase_mark(4, st);
   // ---- 5: window combination, every instance in one launch
   if (num) {
-    k_msm_combine<C><<<(num + 63) / 64, 64, 0, st>>>(d_inst, d_fin, (uint32_t)num, JS, out);
+    k_msm_combine<C><<<(num + 31) / 32, 32, 0, st>>>(d_inst, d_fin, d_order, (uint32_t)num, JS, hdr, out);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
+  phase_mark(5, st);
   return cudaSuccess;
 }
 
@@ -278,7 +322,6 @@ inline Layout plan(int curve, uint32_t num, const uint64_t* sizes, const uint64_
     m.pre_stride = pre_c > 0 ? pre_stride : 0;
     m.Wr = pre_c > 0 ? 1u : m.W;
     m.red_log = (uint32_t)std::min<int>(msm_reduce_log(curve, sizes[i]), (int)m.c - 1);
-    m.digit_off = L.entries_max;
     L.buckets += (uint64_t)m.Wr << (m.c - 1);
     L.entries_max += (uint64_t)m.W * m.n;
     L.total_points += m.n;
@@ -299,14 +342,40 @@ cudaError_t msm_points(int curve, uint32_t num, const uint64_t* offsets, const u
     soff[i] = poff[i];
   }
   Layout L = plan(curve, num, sizes.data(), poff.data(), soff.data(), nullptr);
-  Scratch bases;
-  cudaError_t e = bases.alloc(std::max<uint64_t>(total, 1) * 2 * F::N * 4, st);
-  if (e != cudaSuccess) return e;
-  if (total) {
-    k_points_to_mont<C><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
-        points + offsets[0] * 2 * F::N, total, bases.as<uint32_t>());
-  }
-  return run_set<C>(curve, L, bases.as<uint32_t>(), scalars + offsets[0] * 8, out, st);
+  (void)total;
+  return run_set<C>(curve, L, nullptr, scalars + offsets[0] * 8, out, st, nullptr,
+                    points + offsets[0] * 2 * F::N);
+}
+
+// The uniform per-instance layout of a device-sized batch (window width c, or
+// the library's width for bases with window multiples of width pre_c) with the
+// capacity totals: cap scalar rows in num instances.
+inline Layout plan_uniform(int curve, uint32_t num, int c, uint64_t cap, int pre_c, uint64_t pre_stride) {
+  Layout L;
+  MsmInst m{};
+  m.c = (uint32_t)(pre_c > 0 ? pre_c : c);
+  m.W = (uint32_t)windows_for(curve, (int)m.c);
+  m.Wr = pre_c > 0 ? 1u : m.W;
+  m.pre_stride = pre_c > 0 ? pre_stride : 0;
+  const uint64_t mean = num ? std::max<uint64_t>(cap / num, 2) : 2;
+  m.red_log = (uint32_t)std::min<int>(msm_reduce_log(curve, mean), (int)m.c - 1);
+  L.inst.assign(num, m);
+  for (uint32_t i = 0; i < num; ++i) L.inst[i].bucket_base = (uint32_t)(i * ((uint64_t)m.Wr << (m.c - 1)));
+  L.buckets = (uint64_t)num * ((uint64_t)m.Wr << (m.c - 1));
+  L.entries_max = cap * m.W;
+  L.total_points = cap;
+  L.n_chunks = (L.entries_max + kAccChunk - 1) / kAccChunk;
+  return L;
+}
+
+// Ragged MSMs over caller points with device offsets[num + 1] (offsets[0] = 0),
+// at most cap rows, one window width c for every instance.
+template <class C>
+cudaError_t msm_points_dev(int curve, uint32_t num, uint64_t cap, const uint64_t* offsets, int c,
+                           const uint32_t* points, const uint32_t* scalars, uint32_t* out, cudaStream_t st) {
+  Layout L = plan_uniform(curve, num, c, cap, 0, 0);
+  DevRows dev{offsets, 0, 0, cap};
+  return run_set<C>(curve, L, nullptr, scalars, out, st, &dev, points);
 }
 
 
@@ -363,6 +432,17 @@ cudaError_t precompute_t(Bases* bs, int c, cudaStream_t st) {
   bs->pre = pre;
   bs->pre_c = c;
   return cudaSuccess;
+}
+
+// Ragged MSMs over resident bases with device sizes[num] (scalar rows back to
+// back, at most cap in all), one window width for every instance (the table's
+// when the handle has window multiples, else c).
+template <class C>
+cudaError_t msm_bases_dev_t(Bases* bs, uint32_t num, uint64_t cap, const uint64_t* sizes, int c,
+                            const uint32_t* scalars, uint32_t* out, cudaStream_t st) {
+  Layout L = plan_uniform(bs->curve, num, c, cap, bs->pre ? bs->pre_c : 0, bs->n);
+  DevRows dev{sizes, 1, bs->n, cap};
+  return run_set<C>(bs->curve, L, bs->pre ? bs->pre : bs->mont, scalars, out, st, &dev);
 }
 
 template <class C>

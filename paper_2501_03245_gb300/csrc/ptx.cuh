@@ -86,5 +86,7 @@ ECC_DEV void cp_async16(void* smem, const void* gmem) {
 }
 ECC_DEV void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 ECC_DEV void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+// all but the most recently committed group
+ECC_DEV void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 }  // namespace ptx

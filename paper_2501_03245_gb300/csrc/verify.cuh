@@ -347,7 +347,9 @@ struct FinalRound {
   }
 };
 
-template <class C, int BLOCK>
+// CL > 1: launched in clusters of CL CTAs that share each round's inversion
+// (cta_invert); every CTA runs the same rounds, as that requires.
+template <class C, int BLOCK, int CL = 1>
 __global__ void __launch_bounds__(BLOCK, kGasResidentThreads / BLOCK) k_verify(VerifyArgs<C> a) {
   using Fp = typename C::Fp;
   using Fn = typename C::Fn;
@@ -360,49 +362,49 @@ __global__ void __launch_bounds__(BLOCK, kGasResidentThreads / BLOCK) k_verify(V
   verify_prep<C, BLOCK>(a, begin, end);
   {
     ScalarRound<C> rd{&a};
-    batch_round<Fn, BLOCK>(rd, begin, end, SoA<Fn>{a.M.vec, a.M.stride}, sm);
+    batch_round<Fn, BLOCK, CL>(rd, begin, end, SoA<Fn>{a.M.vec, a.M.stride}, sm);
   }
   {
     TableRound<C, 2, 1> r1{&a};
-    batch_round<Fp, BLOCK>(r1, begin, end, a.M, sm);
+    batch_round<Fp, BLOCK, CL>(r1, begin, end, a.M, sm);
     TableRound<C, 3, 2> r2{&a};
-    batch_round<Fp, BLOCK>(r2, begin, end, a.M, sm);
+    batch_round<Fp, BLOCK, CL>(r2, begin, end, a.M, sm);
     TableRound<C, 5, 4> r3{&a};
-    batch_round<Fp, BLOCK>(r3, begin, end, a.M, sm);
+    batch_round<Fp, BLOCK, CL>(r3, begin, end, a.M, sm);
     if (kQTable >= 16) {
       TableRound<C, 9, 4> r4{&a};
-      batch_round<Fp, BLOCK>(r4, begin, end, a.M, sm);
+      batch_round<Fp, BLOCK, CL>(r4, begin, end, a.M, sm);
       TableRound<C, 13, 4> r5{&a};
-      batch_round<Fp, BLOCK>(r5, begin, end, a.M, sm);
+      batch_round<Fp, BLOCK, CL>(r5, begin, end, a.M, sm);
     }
     if (kQTable >= 32) {
       TableRound<C, 17, 4> r6{&a};
-      batch_round<Fp, BLOCK>(r6, begin, end, a.M, sm);
+      batch_round<Fp, BLOCK, CL>(r6, begin, end, a.M, sm);
       TableRound<C, 21, 4> r7{&a};
-      batch_round<Fp, BLOCK>(r7, begin, end, a.M, sm);
+      batch_round<Fp, BLOCK, CL>(r7, begin, end, a.M, sm);
       TableRound<C, 25, 4> r8{&a};
-      batch_round<Fp, BLOCK>(r8, begin, end, a.M, sm);
+      batch_round<Fp, BLOCK, CL>(r8, begin, end, a.M, sm);
       TableRound<C, 29, 4> r9{&a};
-      batch_round<Fp, BLOCK>(r9, begin, end, a.M, sm);
+      batch_round<Fp, BLOCK, CL>(r9, begin, end, a.M, sm);
     }
   }
   for (int w = kQDigits - 1; w >= 0; --w) {
     if (w < kQDigits - 1) {
       for (int k = 0; k < kQW; ++k) {
         DblRound<C> rd{&a};
-        batch_round<Fp, BLOCK>(rd, begin, end, a.M, sm);
+        batch_round<Fp, BLOCK, CL>(rd, begin, end, a.M, sm);
       }
     }
     if (w < 32) {  // G-table window jg = w rides along
       AddRound<C, true> rd{&a, w, w};
-      batch_round<Fp, BLOCK>(rd, begin, end, a.M, sm);
+      batch_round<Fp, BLOCK, CL>(rd, begin, end, a.M, sm);
     } else {
       AddRound<C, false> rd{&a, w, 0};
-      batch_round<Fp, BLOCK>(rd, begin, end, a.M, sm);
+      batch_round<Fp, BLOCK, CL>(rd, begin, end, a.M, sm);
     }
   }
   FinalRound<C> rf{&a};
-  batch_round<Fp, BLOCK>(rf, begin, end, a.M, sm);
+  batch_round<Fp, BLOCK, CL>(rf, begin, end, a.M, sm);
 }
 
 }  // namespace ecc

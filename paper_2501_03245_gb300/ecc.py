@@ -56,6 +56,16 @@ _SIGS = {
     "ecc_msm_window": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t]),
     "ecc_msm_set_window": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "ecc_msm_reduce_chunk": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t]),
+    "ecc_set_phase_timing": (ctypes.c_int, [ctypes.c_int]),
+    "ecc_set_gas_cluster": (ctypes.c_int, [ctypes.c_int]),
+    "ecc_msm_ragged_dev": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t, ctypes.c_size_t] +
+                           [ctypes.c_void_p] * 4 + [ctypes.c_int, ctypes.c_void_p]),
+    "ecc_msm_bases_ragged_dev": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_size_t] +
+                                 [ctypes.c_void_p] * 4),
+    "ecc_sync_status": (ctypes.c_int, [ctypes.c_void_p]),
+    "ecc_set_allocator": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "ecc_validate_points": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t] + [ctypes.c_void_p] * 3),
+    "ecc_msm_phase_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "ecc_msm_set_reduce_chunk": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "ecc_bench_imad": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "ecc_bench_inv": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_size_t, ctypes.c_int,
@@ -267,6 +277,68 @@ def ecc_msm_reduce_chunk(curve, n):
 
 def ecc_msm_set_reduce_chunk(curve, log2_n, log2_chunk):
     return _check(load().ecc_msm_set_reduce_chunk(curve, log2_n, log2_chunk))
+
+
+def ecc_msm_ragged_dev(curve, num, max_points, offsets, points, scalars, out, c=0, stream=None):
+    """offsets: device tensor of num + 1 uint64 row indices (offsets[0] = 0)."""
+    return _check(load().ecc_msm_ragged_dev(curve, num, max_points, _ptr(offsets), _ptr(points),
+                                            _ptr(scalars), _ptr(out), c, _stream(stream)))
+
+
+def ecc_msm_bases_ragged_dev(handle, num, max_points, sizes, scalars, out, stream=None):
+    """sizes: device tensor of num uint64 instance sizes."""
+    return _check(load().ecc_msm_bases_ragged_dev(handle, num, max_points, _ptr(sizes), _ptr(scalars),
+                                                  _ptr(out), _stream(stream)))
+
+
+def ecc_sync_status(stream=None):
+    """Synchronises the stream and raises EccError if a kernel recorded an error."""
+    return _check(load().ecc_sync_status(_stream(stream)))
+
+
+# ctypes prototypes of the allocator hook (kept referenced while installed)
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+_hooks = []
+
+
+def ecc_set_allocator(alloc=None, release=None):
+    """Installs Python callables alloc(bytes, stream) -> int pointer and
+    release(ptr, stream) as the workspace allocator (None, None: default)."""
+    if alloc is None:
+        rc = _check(load().ecc_set_allocator(None, None, None))
+        _hooks.clear()
+        return rc
+    fa = ALLOC_FN(lambda b, s, ctx: alloc(b, s or 0) or None)
+    fr = FREE_FN(lambda p, s, ctx: release(p, s or 0))
+    rc = _check(load().ecc_set_allocator(ctypes.cast(fa, ctypes.c_void_p), ctypes.cast(fr, ctypes.c_void_p),
+                                         None))
+    _hooks[:] = [fa, fr]
+    return rc
+
+
+def ecc_validate_points(curve, n, points, ok_out, stream=None):
+    return _check(load().ecc_validate_points(curve, n, _ptr(points), _ptr(ok_out), _stream(stream)))
+
+
+MSM_PHASES = ("sort", "accumulate", "fold", "reduce", "combine")
+
+
+def ecc_set_gas_cluster(ctas):
+    return _check(load().ecc_set_gas_cluster(int(ctas)))
+
+
+def ecc_set_phase_timing(on):
+    return _check(load().ecc_set_phase_timing(int(bool(on))))
+
+
+def ecc_msm_phase_times():
+    """{phase name: device ms} of this thread's last timed MSM call."""
+    buf = (ctypes.c_float * len(MSM_PHASES))()
+    k = load().ecc_msm_phase_times(ctypes.addressof(buf), len(MSM_PHASES))
+    if k < 0:
+        _check(k)
+    return {MSM_PHASES[i]: float(buf[i]) for i in range(k)}
 
 
 def ecc_bench_imad(threads, iters, sink, stream=None):

@@ -38,6 +38,8 @@ def test_verify_count_structure():
     assert m == 259 * 7 + 96 * 6 + 7 + 9
     assert costmodel.verify_imad() == m * 136
     assert costmodel.fpmul_modmul() == 32 * 6
+    # signing: k G and d G ride the same 32 comb rounds, then s = k^-1 (e + r d)
+    assert costmodel.sign_modmul() == 2 * costmodel.fpmul_modmul() + costmodel.SIGN_SCALAR_MODMUL
 
 
 def test_verify_schedule_matches_the_kernel():

@@ -123,3 +123,29 @@ def test_summary_percentiles_are_nearest_rank():
     assert s["mean_ms"] == pytest.approx(50.5)
     assert s["throughput_req_s"] == pytest.approx(50.0)
     assert s["verify_triples_s"] == pytest.approx(250.0) and s["msm_points_s"] == pytest.approx(250.0)
+
+
+def test_round_admission_by_workspace_and_ring_contiguity():
+    """A round takes waiting requests in arrival order while their payloads are
+    contiguous in the ring, within the item limit and the workspace budget; a
+    request whose workspace does not fit what is left waits."""
+    R = serving.Request
+    reqs = [R(0, "verify", 100, 0.0, 0), R(1, "verify", 50, 0.0, 100), R(2, "verify", 30, 0.0, 150),
+            R(3, "verify", 40, 0.0, 0)]                       # the ring wrapped before request 3
+    cost = lambda items: 1000 + 10 * items  # noqa: E731
+    batch, items = serving.take_round(reqs, 1 << 20, 10 ** 9, cost)
+    assert [q.rid for q in batch] == [0, 1, 2] and items == 180
+    batch, _ = serving.take_round(reqs, 160, 10 ** 9, cost)    # item limit
+    assert [q.rid for q in batch] == [0, 1]
+    batch, _ = serving.take_round(reqs, 1 << 20, cost(150), cost)  # budget: the third does not fit
+    assert [q.rid for q in batch] == [0, 1]
+    batch, items = serving.take_round(reqs, 1 << 20, cost(99), cost)  # not even the first: wait
+    assert batch == [] and items == 0
+
+
+def test_request_work_follows_the_cost_model():
+    v = serving.request_work("verify", 10, 16)
+    assert v == 10 * costmodel.verify_imad()
+    m = serving.request_work("msm", 1 << 12, 16)
+    W = costmodel.msm_windows(254, 16)
+    assert m == costmodel.msm_modmul_precomputed(1 << 12, W, 16) * 136
