@@ -307,14 +307,14 @@ int ecc_msm_set_window(ecc_curve_t curve, int log2_n, int c);
 int ecc_msm_reduce_chunk(ecc_curve_t curve, size_t n);
 int ecc_msm_set_reduce_chunk(ecc_curve_t curve, int log2_n, int log2_chunk);
 
-/* Gather-apply-scatter across a thread-block cluster for P-256 verification
+/* Gather-apply-scatter across a thread-block cluster for ECDSA verification
  * (the memory-management idea of Section 3.3 taken to a cluster): with ctas =
- * 2 or 4, ecc_verify_batch on P-256 runs in clusters of that many CTAs that
- * share each round's single inversion through distributed shared memory (the
- * other CTAs' products go to the first, which inverts their product by
- * Montgomery's trick and sends each its inverse back); ctas = 1 gives every
- * CTA its own inversion.  Process-wide setting; results are identical for
- * every value; other values give ECC_EINVAL. */
+ * 2 (the default), ecc_verify_batch runs in clusters of two CTAs that share
+ * each round's single inversion through distributed shared memory (the second
+ * CTA's product goes to the first, which inverts both products by Montgomery's
+ * trick and sends the second its inverse back); ctas = 1 gives every CTA its
+ * own inversion.  Process-wide setting; results are identical either way;
+ * other values give ECC_EINVAL. */
 int ecc_set_gas_cluster(int ctas);
 
 /* MSM phase timers (diagnostics).  With timing on, every MSM entry point

@@ -686,7 +686,7 @@ int ecc_msm_set_reduce_chunk(ecc_curve_t curve, int log2_n, int log2_chunk) {
 }
 
 int ecc_set_gas_cluster(int ctas) {
-  if (ctas != 1 && ctas != 2 && ctas != 4) return fail(ECC_EINVAL, "ecc_set_gas_cluster: ctas must be 1, 2 or 4");
+  if (ctas != 1 && ctas != 2) return fail(ECC_EINVAL, "ecc_set_gas_cluster: ctas must be 1 or 2");
   set_gas_cluster(ctas);
   return ok();
 }

@@ -70,8 +70,8 @@ cudaError_t launch_validate_points(int curve, size_t n, const uint32_t* p, uint8
 // Montgomery (x block then y block).
 cudaError_t gtable(int curve, const uint4** table, cudaStream_t st);
 
-// P-256 verification in clusters of `ctas` (1, 2 or 4) CTAs sharing each
-// round's inversion
+// ECDSA verification in clusters of `ctas` (1 or 2) CTAs sharing each round's
+// inversion
 void set_gas_cluster(int ctas);
 
 // FPMUL k_i G (scalars n x 8 LE limbs; out n x 2N LE limbs)

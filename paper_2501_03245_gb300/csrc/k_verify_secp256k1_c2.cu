@@ -1,0 +1,12 @@
+// Batched ECDSA verification kernel instantiated for one curve and cluster
+// size (a translation unit per instantiation so the library builds in parallel).
+#include "verify_host.cuh"
+
+namespace ecc {
+
+cudaError_t verify_secp256k1_c2(size_t n, const uint8_t* hash, const uint8_t* r, const uint8_t* s,
+                           const uint8_t* pub, uint8_t* ok, cudaStream_t st) {
+  return verify_detail::verify<Secp256k1, 2>(n, hash, r, s, pub, ok, st, 0);
+}
+
+}  // namespace ecc

@@ -4,9 +4,9 @@
 
 namespace ecc {
 
-cudaError_t verify_p256_c4(size_t n, const uint8_t* hash, const uint8_t* r, const uint8_t* s,
+cudaError_t verify_sm2_c2(size_t n, const uint8_t* hash, const uint8_t* r, const uint8_t* s,
                            const uint8_t* pub, uint8_t* ok, cudaStream_t st) {
-  return verify_detail::verify<P256, 4>(n, hash, r, s, pub, ok, st, 1);
+  return verify_detail::verify<SM2, 2>(n, hash, r, s, pub, ok, st, 4);
 }
 
 }  // namespace ecc

@@ -106,26 +106,27 @@ def test_verify_ragged_sets_in_a_cuda_graph(gpu_lib):
         assert np.array_equal(from_cuda(ok), cpp_oracle.verify(cid, *x))
 
 
-@pytest.mark.parametrize("ctas", [1, 2, 4])
+@pytest.mark.parametrize("cid", [0, 1, 4])
+@pytest.mark.parametrize("ctas", [1, 2])
 @pytest.mark.parametrize("n", [5000, 77])
-def test_verify_p256_cluster_gas(gpu_lib, n, ctas):
-    """P-256 verification with the CTAs of a cluster sharing each round's
-    inversion (ecc_set_gas_cluster) gives the oracle's bits for every cluster
-    size; 77 triples leave all but one CTA of the cluster without items."""
-    e, r, s, pub = make_triples(1, n, 0x6ECC4100 + n, 16)
-    e, r, s, pub = add_malformed(1, e, r, s, pub)
-    want = cpp_oracle.verify(1, e, r, s, pub)
+def test_verify_cluster_gas(gpu_lib, n, ctas, cid):
+    """Verification with one inversion per CTA and with the two CTAs of a
+    cluster sharing each round's inversion (ecc_set_gas_cluster) gives the
+    oracle's bits; 77 triples leave the second CTA of the pair without items."""
+    e, r, s, pub = make_triples(cid, n, 0x6ECC4100 + n + cid, 16)
+    e, r, s, pub = add_malformed(cid, e, r, s, pub)
+    want = cpp_oracle.verify(cid, e, r, s, pub)
     from paper_2501_03245_gb300 import ecc
 
     gpu_lib.ecc_set_gas_cluster(ctas)
     try:
-        got = run_gpu(gpu_lib, 1, e, r, s, pub)
+        got = run_gpu(gpu_lib, cid, e, r, s, pub)
     finally:
         gpu_lib.ecc_set_gas_cluster(DEFAULT_GAS_CLUSTER)
     assert np.array_equal(got, want)
     with pytest.raises(ecc.EccError):
-        gpu_lib.ecc_set_gas_cluster(3)
+        gpu_lib.ecc_set_gas_cluster(4)
 
 
-# the library's default cluster size for P-256 verification
-DEFAULT_GAS_CLUSTER = 1
+# the library's default cluster size for verification
+DEFAULT_GAS_CLUSTER = 2
