@@ -351,8 +351,10 @@ int ecc_bench_modmul(ecc_curve_t curve, int reduction, size_t threads, int iters
 
 /* Inversion latency probe: each thread runs a chain of `iters` dependent
  * inversions in the curve's base field, method 0 = Fermat (Section 2.2),
- * 1 = divsteps (the GAS apply step).  With threads = 1 the kernel time / iters
- * is the latency of one inversion on one thread. */
+ * 1 = the GAS apply step's (branch-free single divsteps on 30-bit limbs),
+ * 2 = batched variable-time divsteps on 62-bit limbs, 3 = the same on 30-bit
+ * limbs.  With threads = 1 the kernel time / iters is the latency of one
+ * inversion on one thread. */
 int ecc_bench_inv(ecc_curve_t curve, int method, size_t threads, int iters, uint32_t* sink,
                   void* stream);
 

@@ -749,7 +749,7 @@ int ecc_fp_inv_batch_noalloc(ecc_curve_t curve, int field, size_t n, const uint3
 int ecc_bench_inv(ecc_curve_t curve, int method, size_t threads, int iters, uint32_t* sink,
                   void* stream) {
   if (!valid_curve(curve)) return fail(ECC_EINVAL, "ecc_bench_inv: unknown curve");
-  if ((method != 0 && method != 1) || threads == 0 || iters < 0 || !sink)
+  if (method < 0 || method > 3 || threads == 0 || iters < 0 || !sink)
     return fail(ECC_EINVAL, "ecc_bench_inv: bad argument");
   cudaError_t e = launch_bench_inv(curve, method, threads, iters, sink, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "ecc_bench_inv");

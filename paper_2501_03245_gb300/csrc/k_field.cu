@@ -136,8 +136,12 @@ __global__ void k_bench_inv(int method, int iters, uint32_t* sink) {
   for (int it = 0; it < iters; ++it) {
     if (method == 0) {
       fe_inv_fermat<F>(x, x);
-    } else {
+    } else if (method == 1) {
       fe_inv_mont<F>(x, x);
+    } else if (method == 2) {
+      fe_inv_mont62<F>(x, x);
+    } else {
+      fe_inv_mont<F, false>(x, x);
     }
     x[0] ^= 1u;  // never a fixed point
   }

@@ -143,3 +143,36 @@ def test_bench_modmul_reductions(gpu_lib):
     torch.cuda.synchronize()
     with pytest.raises(ecc.EccError):
         gpu_lib.ecc_bench_modmul(3, 1, 512, 4, sink)
+
+
+@pytest.mark.parametrize("cid", [0, 1, 2, 3, 4])
+def test_bench_inv_methods_match_the_oracle(gpu_lib, cid):
+    """The inversion probe runs a chain of dependent inversions in Montgomery
+    form (a = xR -> x^-1 R, then flip bit 0) per thread: Fermat, the 30-bit
+    divsteps of the GAS apply step and the 62-bit divsteps end on the oracle's
+    chain, folded to one word per thread."""
+    import torch
+
+    C = curves.BY_ID[cid]
+    q, N = C.p, C.limbs
+    R = 1 << (32 * N)
+    threads, iters = 70, 9
+    one = synth.ints_to_limbs([R % q], N)[0]
+    want = []
+    for t in range(threads):
+        w = [int(one[k]) ^ ((t * 2654435761 + k) & 0xFFFFFFFF) for k in range(N)]
+        w[N - 1] &= 0x0FFFFFFF
+        a = sum(v << (32 * k) for k, v in enumerate(w))
+        for _ in range(iters):
+            a = field.mul(q, R * R % q, field.inv(q, a)) if a % q else 0
+            a ^= 1
+        fold = 0
+        for k in range(N):
+            fold ^= (a >> (32 * k)) & 0xFFFFFFFF
+        want.append(fold)
+    for method in (0, 1, 2, 3):
+        sink = torch.zeros(threads, dtype=torch.int32, device="cuda")
+        gpu_lib.ecc_bench_inv(cid, method, threads, iters, sink)
+        torch.cuda.synchronize()
+        got = [int(v) & 0xFFFFFFFF for v in sink.cpu().tolist()]
+        assert got == want, method
