@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-msm", action="store_true", help="skip the MSM and ragged-MSM lines")
     ap.add_argument("--no-ragged", action="store_true", help="skip the ragged-MSM line")
+    ap.add_argument("--no-table-msm", action="store_true",
+                    help="skip the BLS12-381 resident-bases MSM line (keep the ragged line)")
     ap.add_argument("--no-sm2", action="store_true", help="skip the SM2 verification line")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the secp256k1 4096-triple and the SM2 signing / FPMUL lines")
@@ -79,6 +81,20 @@ def dist_env():
     return world, rank, local
 
 
+def _nvtx(name):
+    """Each line's timed region is an NVTX range named after the line (ncu
+    --nvtx --nvtx-include "<name>/" profiles only launches inside it)."""
+    try:
+        import torch
+
+        if name is None:
+            torch.cuda.nvtx.range_pop()
+        else:
+            torch.cuda.nvtx.range_push(name)
+    except Exception:
+        pass
+
+
 class ClockSampler:
     """SM clocks and throttle reasons during timed regions: one background
     `nvidia-smi -lms 200` for the whole run (started once, before the first
@@ -107,9 +123,11 @@ class ClockSampler:
 
     def begin(self, name):
         self.windows[name] = [time.time(), None]
+        _nvtx(name)
 
     def end(self, name):
         self.windows[name][1] = time.time()
+        _nvtx(None)
 
     def stop(self):
         time.sleep(0.3)
@@ -152,10 +170,10 @@ class ClockSampler:
 
 class _NoClock:
     def begin(self, name):
-        pass
+        _nvtx(name)
 
     def end(self, name):
-        pass
+        _nvtx(None)
 
     def summary(self, name):
         return None
@@ -193,9 +211,9 @@ def gen_inputs(ecc, synth, torch, n, seed, curve=CURVE_P256):
 # DRAM traffic of one k_verify launch over 2^20 P-256 triples (dram__bytes_read.sum +
 # dram__bytes_write.sum, from one ncu capture), valid only for the kernel sources
 # it was taken on: the digest of those sources must match, else it is null.
-VERIFY_TRAFFIC = {"bytes": 82872315136 + 34264189184, "batch": 1 << 20, "digest": "c4acca0c4152fa37",
+VERIFY_TRAFFIC = {"bytes": 79369814528 + 33884342528, "batch": 1 << 20, "digest": "d56ffe9d83e1591f",
                   "sources": ["verify.cuh", "verify_host.cuh", "ops.cuh", "ec.cuh", "fp.cuh", "inv.cuh",
-                              "ptx.cuh", "curves_gen.cuh", "internal.h", "k_verify_p256.cu"]}
+                              "ptx.cuh", "curves_gen.cuh", "internal.h", "k_verify_p256_c2.cu", "k_verify.cu"]}
 
 
 def verify_traffic(n):
@@ -379,17 +397,16 @@ def bench_sm2(ecc, costmodel, synth, torch, peak, rank, n, steps, world=1, clk=N
 def bench_ragged(ecc, costmodel, synth, torch, peak, rank, world=1, clk=None, reps=10):
     """BN254 ragged batch: 256 MSMs with log-uniform sizes 2^10..2^18, all in one
     launch sequence captured once in a CUDA graph and replayed, against one
-    launch sequence per MSM.  Window width and the reduction's bucket layout
-    are autotuned per size class.  The algorithmic work is the sum of every
-    instance's Pippenger count at the window width the library picks for its
-    size."""
+    launch sequence per MSM.  Window widths are autotuned per size class, then
+    a common width shift and the reduction's bucket layout on this batch.  The
+    algorithmic work is the sum of every instance's Pippenger count at the
+    window width the library picks for its size."""
     from paper_2501_03245_gb300 import autotune
 
     clk = clk or _NoClock()
     curve = ecc.ECC_BN254
     classes = list(range(10, 19))
     tuned = autotune.tune(curve, classes, torch)  # one window width per size class
-    layout = autotune.tune_layout(curve, classes, torch)  # and one reduction chunk
     seed = synth.SEED_BASE + 3 + 1000 * rank
     sizes = synth.ragged_sizes(seed, 256)
     total = int(sizes.sum())
@@ -399,6 +416,9 @@ def bench_ragged(ecc, costmodel, synth, torch, peak, rank, world=1, clk=None, re
     sc = torch.from_numpy(ks[0].view("int32")).cuda()
     offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
     out = torch.empty((256, 16), dtype=torch.int32, device="cuda")
+    # the knobs the instances share (a common width shift, the reduction
+    # chunk) tuned on this batch, untimed
+    layout = autotune.tune_batch(curve, classes, lambda: ecc.ecc_msm_ragged(curve, 256, offs, pts, sc, out), torch)
     ecc.ecc_msm_ragged(curve, 256, offs, pts, sc, out)
     torch.cuda.synchronize()
     ref = out.clone()
@@ -425,8 +445,9 @@ def bench_ragged(ecc, costmodel, synth, torch, peak, rank, world=1, clk=None, re
     per = _event_time(torch, lambda: [ecc.ecc_msm(curve, int(sizes[i]), pts[int(offs[i]):int(offs[i + 1])],
                                                   sc[int(offs[i]):int(offs[i + 1])], one)
                                       for i in range(256)], 1)
-    # the graph rate stands only when its replay reproduced the eager result
-    best = graph if (graph and graph_ok is True) else eager
+    # the faster of the two forms; the graph's only when its replay reproduced
+    # the eager result
+    best = graph if (graph and graph_ok is True and graph <= eager) else eager
     widths = [ecc.ecc_msm_window(curve, int(k)) for k in sizes]
     alg = sum(costmodel.msm_modmul(int(k), costmodel.msm_windows(254, c), c) for k, c in zip(sizes, widths))
     alg *= costmodel.imad_per_modmul(8)
@@ -436,7 +457,8 @@ def bench_ragged(ecc, costmodel, synth, torch, peak, rank, world=1, clk=None, re
             "form": "graph replay" if best is graph else "eager",
             "graph_replay_ms": graph * 1e3 if graph else None, "eager_ms": eager * 1e3,
             "graph_bit_equal": graph_ok, "timed_calls": reps, "clocks": clk.summary("ragged"),
-            "autotuned": {str(k): {"c": v, "reduce_chunk_log2": layout.get(k)} for k, v in sorted(tuned.items())},
+            "autotuned": {"c": {str(k): ecc.ecc_msm_window(curve, 1 << k) for k in sorted(tuned)},
+                          "batch": layout},
             "phases_ms": phases, "sort": _sort_line(phases, total, digits),
             "plain": {"value": job_rate(total, per, world), "unit": "points/s",
                       "form": "one launch sequence per MSM", "frac": alg / per / peak},
@@ -678,7 +700,7 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic",
         "config": verify_config(n), "valid_signatures": n_valid,
-        "roofline": {"bound": "alu", "kernel": "k_verify<P256>", "achieved": achieved / 1e12,
+        "roofline": {"bound": "alu", "kernel": "k_verify<P256, 256, 2>", "achieved": achieved / 1e12,
                      "peak": peak / 1e12, "unit": "T IMAD.WIDE/s", "frac": achieved / peak,
                      "traffic": verify_traffic(n), "traffic_unit": "DRAM bytes per launch",
                      "basis": f"{costmodel.verify_modmul()} modmul x 136 wide mul-adds per verify; "
@@ -690,8 +712,9 @@ def run_ours(args):
     }
     del e, r, s, pub, ok, e_h, r_h, s_h, p_h, ok_h
     if not args.no_msm:
-        line["msm"] = bench_msm(ecc, costmodel, synth, torch, peak, rank, args.msm_n, args.msm_vectors,
-                                world, clk)
+        if not args.no_table_msm:
+            line["msm"] = bench_msm(ecc, costmodel, synth, torch, peak, rank, args.msm_n, args.msm_vectors,
+                                    world, clk)
         if not args.no_ragged:
             line["ragged"] = bench_ragged(ecc, costmodel, synth, torch, peak, rank, world, clk)
     if not args.no_sm2:

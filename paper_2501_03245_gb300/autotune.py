@@ -43,6 +43,25 @@ def time_msm(curve, bases, scalars, n, torch, reps=3):
     return a.elapsed_time(b) / reps / 1e3
 
 
+def time_msm_batch(curve, bases, scalars, n, batch_points, torch, reps=3):
+    """Time of one ecc_msm_ragged call of max(1, batch_points // n) instances of
+    n points each (the shape of a batch, where the launches are shared)."""
+    import numpy as np
+
+    m = max(1, batch_points // n)
+    offs = np.arange(m + 1, dtype=np.uint64) * n
+    out = torch.empty((m, 2 * ecc.ecc_limbs(curve)), dtype=torch.int32, device="cuda")
+    ecc.ecc_msm_ragged(curve, m, offs, bases, scalars, out)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        ecc.ecc_msm_ragged(curve, m, offs, bases, scalars, out)
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps / 1e3
+
+
 def time_msm_bases(curve, bases, scalars, n, vectors, torch, reps=3):
     """Time of one ecc_msm_bases call over `vectors` scalar vectors of n."""
     h = ecc.ecc_bases_create(curve, n, bases)
@@ -89,10 +108,12 @@ def tune_precomputed(handle, vectors, scalars, torch, candidates, reps=3):
     return best, times
 
 
-def tune(curve, log2_sizes, torch, spread=2, seed=0x6ECC7777, cache=None, vectors=1):
+def tune(curve, log2_sizes, torch, spread=2, seed=0x6ECC7777, cache=None, vectors=1, batch_points=0):
     """Returns {log2_n: c} and installs it in the library.  With vectors > 1
     every candidate is timed on the resident-bases form with that many scalar
-    vectors per call (the best window grows with the vectors sharing a call)."""
+    vectors per call (the best window grows with the vectors sharing a call);
+    with batch_points > 0 on ragged calls of equal instances of the class's
+    size, about batch_points points in all (the shape of a batch)."""
     key = None
     table = {}
     if cache and os.path.exists(cache):
@@ -101,7 +122,7 @@ def tune(curve, log2_sizes, torch, spread=2, seed=0x6ECC7777, cache=None, vector
         table = {int(k): int(v) for k, v in saved.items()}
     missing = [l for l in log2_sizes if l not in table]
     if missing:
-        n_max = 1 << max(missing)
+        n_max = max(1 << max(missing), batch_points)
         bases = make_bases(curve, n_max, seed, torch)
         ks = synth.uniform_limbs(seed, synth.S_SCALAR, n_max * vectors, _curve_order(curve))
         scalars = torch.from_numpy(ks.view("int32")).cuda()
@@ -114,6 +135,8 @@ def tune(curve, log2_sizes, torch, spread=2, seed=0x6ECC7777, cache=None, vector
                 ecc.ecc_msm_set_window(curve, l, c)
                 if vectors > 1:
                     t = time_msm_bases(curve, bases, scalars[:n * vectors].contiguous(), n, vectors, torch)
+                elif batch_points:
+                    t = time_msm_batch(curve, bases, scalars, n, batch_points, torch)
                 else:
                     t = time_msm(curve, bases, scalars, n, torch)
                 if best is None or t < best[0]:
@@ -173,3 +196,53 @@ def tune_layout(curve, log2_sizes, torch, candidates=(3, 4, 5, 6), seed=0x6ECC77
         table[l] = best[1]
         ecc.ecc_msm_set_reduce_chunk(curve, l, best[1])
     return table
+
+
+def tune_batch(curve, log2_sizes, run, torch, shifts=(-1, 0, 1), chunks=(3, 4, 5), reps=3):
+    """Tunes the knobs that one ragged launch sequence shares across its
+    instances on the batch itself: run() makes the caller's ecc_msm_ragged call.
+
+    The first-level reduction of all instances runs in one launch whose round
+    count is set by the largest chunk in it, so a per-class chunk choice made
+    on batches of one size does not transfer to a mix; likewise the window
+    widths of the classes interact through the shared launches.  So, starting
+    from the per-class widths already installed (tune), every width is shifted
+    by the same s (each in [2, 20]) for each s in shifts, then one chunk 2^k
+    (capped at c - 1 per class) is set for every class for each k in chunks;
+    each candidate is timed as reps calls of run(), the fastest is installed.
+    Returns {"shift": s, "chunk_log2": k, "ms": {...}}."""
+    base = {l: ecc.ecc_msm_window(curve, 1 << l) for l in log2_sizes}
+
+    def timed():
+        run()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            run()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    def set_shift(s):
+        for l, c in base.items():
+            ecc.ecc_msm_set_window(curve, l, min(20, max(2, c + s)))
+
+    def set_chunk(k):
+        for l in log2_sizes:
+            c = ecc.ecc_msm_window(curve, 1 << l)
+            ecc.ecc_msm_set_reduce_chunk(curve, l, max(1, min(k, c - 1)))
+
+    ms = {}
+    set_chunk(chunks[len(chunks) // 2])
+    for s in shifts:
+        set_shift(s)
+        ms[f"shift {s}"] = timed()
+    shift = min(shifts, key=lambda s: ms[f"shift {s}"])
+    set_shift(shift)
+    for k in chunks:
+        set_chunk(k)
+        ms[f"chunk {k}"] = timed()
+    chunk = min(chunks, key=lambda k: ms[f"chunk {k}"])
+    set_chunk(chunk)
+    return {"shift": shift, "chunk_log2": chunk, "ms": {k: round(v, 3) for k, v in ms.items()}}
