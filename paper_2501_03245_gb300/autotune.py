@@ -198,7 +198,7 @@ def tune_layout(curve, log2_sizes, torch, candidates=(3, 4, 5, 6), seed=0x6ECC77
     return table
 
 
-def tune_batch(curve, log2_sizes, run, torch, shifts=(-1, 0, 1), chunks=(3, 4, 5), reps=3):
+def tune_batch(curve, log2_sizes, run, torch, shifts=(-1, 0, 1), chunks=(3, 4, 5), reps=3, min_gain=0.005):
     """Tunes the knobs that one ragged launch sequence shares across its
     instances on the batch itself: run() makes the caller's ecc_msm_ragged call.
 
@@ -210,7 +210,10 @@ def tune_batch(curve, log2_sizes, run, torch, shifts=(-1, 0, 1), chunks=(3, 4, 5
     by the same s (each in [2, 20]) for each s in shifts, then one chunk 2^k
     (capped at c - 1 per class) is set for every class for each k in chunks;
     each candidate is timed as reps calls of run(), the fastest is installed.
-    Returns {"shift": s, "chunk_log2": k, "ms": {...}}."""
+    Last, each group of classes that share a width tries that width - 1 and
+    + 1 on the batch (the others fixed); a change stays when it is faster by
+    more than min_gain.  Returns {"shift": s, "chunk_log2": k, "widths":
+    {log2_n: c}, "ms": {...}}."""
     base = {l: ecc.ecc_msm_window(curve, 1 << l) for l in log2_sizes}
 
     def timed():
@@ -245,4 +248,25 @@ def tune_batch(curve, log2_sizes, run, torch, shifts=(-1, 0, 1), chunks=(3, 4, 5
         ms[f"chunk {k}"] = timed()
     chunk = min(chunks, key=lambda k: ms[f"chunk {k}"])
     set_chunk(chunk)
-    return {"shift": shift, "chunk_log2": chunk, "ms": {k: round(v, 3) for k, v in ms.items()}}
+    best = ms[f"chunk {chunk}"]
+    groups = {}
+    for l in log2_sizes:
+        groups.setdefault(ecc.ecc_msm_window(curve, 1 << l), []).append(l)
+    for c, ls in sorted(groups.items()):
+        for cc in (c - 1, c + 1):
+            if not 2 <= cc <= 20:
+                continue
+            for l in ls:
+                ecc.ecc_msm_set_window(curve, l, cc)
+            set_chunk(chunk)
+            t = timed()
+            ms[f"width {c} -> {cc}"] = t
+            if t < best * (1 - min_gain):
+                best = t
+                break
+            for l in ls:
+                ecc.ecc_msm_set_window(curve, l, c)
+            set_chunk(chunk)
+    widths = {l: ecc.ecc_msm_window(curve, 1 << l) for l in log2_sizes}
+    return {"shift": shift, "chunk_log2": chunk, "widths": widths,
+            "ms": {k: round(v, 3) for k, v in ms.items()}}
