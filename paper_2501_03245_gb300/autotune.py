@@ -6,6 +6,10 @@ fastest, installs it with ``ecc_msm_set_window`` and can persist the table as
 JSON (keyed by GPU name and curve) so a later process reloads it instead of
 measuring again.  Inputs are made on the device by the library itself
 (``ecc_fixed_base_mul`` for the bases), so tuning needs no CPU arithmetic.
+``tune_precomputed`` picks the width of a resident base set's window-multiple
+table; ``tune_batch`` tunes, on a caller's ragged batch itself, the knobs its
+instances share (a common width shift, the first-level reduction chunk, one
+width step per group of classes).
 """
 import json
 import os
@@ -38,25 +42,6 @@ def time_msm(curve, bases, scalars, n, torch, reps=3):
     a.record()
     for _ in range(reps):
         ecc.ecc_msm(curve, n, bases, scalars, out)
-    b.record()
-    torch.cuda.synchronize()
-    return a.elapsed_time(b) / reps / 1e3
-
-
-def time_msm_batch(curve, bases, scalars, n, batch_points, torch, reps=3):
-    """Time of one ecc_msm_ragged call of max(1, batch_points // n) instances of
-    n points each (the shape of a batch, where the launches are shared)."""
-    import numpy as np
-
-    m = max(1, batch_points // n)
-    offs = np.arange(m + 1, dtype=np.uint64) * n
-    out = torch.empty((m, 2 * ecc.ecc_limbs(curve)), dtype=torch.int32, device="cuda")
-    ecc.ecc_msm_ragged(curve, m, offs, bases, scalars, out)
-    torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
-    for _ in range(reps):
-        ecc.ecc_msm_ragged(curve, m, offs, bases, scalars, out)
     b.record()
     torch.cuda.synchronize()
     return a.elapsed_time(b) / reps / 1e3
@@ -108,12 +93,10 @@ def tune_precomputed(handle, vectors, scalars, torch, candidates, reps=3):
     return best, times
 
 
-def tune(curve, log2_sizes, torch, spread=2, seed=0x6ECC7777, cache=None, vectors=1, batch_points=0):
+def tune(curve, log2_sizes, torch, spread=2, seed=0x6ECC7777, cache=None, vectors=1):
     """Returns {log2_n: c} and installs it in the library.  With vectors > 1
     every candidate is timed on the resident-bases form with that many scalar
-    vectors per call (the best window grows with the vectors sharing a call);
-    with batch_points > 0 on ragged calls of equal instances of the class's
-    size, about batch_points points in all (the shape of a batch)."""
+    vectors per call (the best window grows with the vectors sharing a call)."""
     key = None
     table = {}
     if cache and os.path.exists(cache):
@@ -122,7 +105,7 @@ def tune(curve, log2_sizes, torch, spread=2, seed=0x6ECC7777, cache=None, vector
         table = {int(k): int(v) for k, v in saved.items()}
     missing = [l for l in log2_sizes if l not in table]
     if missing:
-        n_max = max(1 << max(missing), batch_points)
+        n_max = 1 << max(missing)
         bases = make_bases(curve, n_max, seed, torch)
         ks = synth.uniform_limbs(seed, synth.S_SCALAR, n_max * vectors, _curve_order(curve))
         scalars = torch.from_numpy(ks.view("int32")).cuda()
@@ -135,8 +118,6 @@ def tune(curve, log2_sizes, torch, spread=2, seed=0x6ECC7777, cache=None, vector
                 ecc.ecc_msm_set_window(curve, l, c)
                 if vectors > 1:
                     t = time_msm_bases(curve, bases, scalars[:n * vectors].contiguous(), n, vectors, torch)
-                elif batch_points:
-                    t = time_msm_batch(curve, bases, scalars, n, batch_points, torch)
                 else:
                     t = time_msm(curve, bases, scalars, n, torch)
                 if best is None or t < best[0]:
@@ -150,51 +131,6 @@ def tune(curve, log2_sizes, torch, spread=2, seed=0x6ECC7777, cache=None, vector
         data[key] = {str(k): v for k, v in sorted(table.items())}
         with open(cache, "w") as f:
             json.dump(data, f, indent=1)
-    return table
-
-
-def tune_layout(curve, log2_sizes, torch, candidates=(3, 4, 5, 6), seed=0x6ECC7778, batch_points=1 << 22):
-    """Bucket layout of the reduction: for every size class (after its window
-    width is set), times a ragged call of equal instances of that size (about
-    batch_points points in all, the shape of a batch, where the reduction's
-    rounds are shared by many instances) with first-level reduction chunks of
-    2^k buckets for each candidate k (capped at c - 1, where a chunk covers a
-    whole bucket row), installs the fastest with ecc_msm_set_reduce_chunk and
-    returns {log2_n: k}."""
-    import numpy as np
-
-    table = {}
-    if not log2_sizes:
-        return table
-    n_max = max(1 << max(log2_sizes), batch_points)
-    bases = make_bases(curve, n_max, seed, torch)
-    ks = synth.uniform_limbs(seed, synth.S_SCALAR, n_max, _curve_order(curve))
-    scalars = torch.from_numpy(ks.view("int32")).cuda()
-    limbs = ecc.ecc_limbs(curve)
-    for l in log2_sizes:
-        n = 1 << l
-        m = max(1, batch_points // n)
-        offs = np.arange(m + 1, dtype=np.uint64) * n
-        out = torch.empty((m, 2 * limbs), dtype=torch.int32, device="cuda")
-        c = ecc.ecc_msm_window(curve, n)
-        best = None
-        for k in sorted({min(k, c - 1) for k in candidates}):
-            if k < 1:
-                continue
-            ecc.ecc_msm_set_reduce_chunk(curve, l, k)
-            ecc.ecc_msm_ragged(curve, m, offs, bases, scalars, out)
-            torch.cuda.synchronize()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
-            for _ in range(3):
-                ecc.ecc_msm_ragged(curve, m, offs, bases, scalars, out)
-            b.record()
-            torch.cuda.synchronize()
-            t = a.elapsed_time(b)
-            if best is None or t < best[0]:
-                best = (t, k)
-        table[l] = best[1]
-        ecc.ecc_msm_set_reduce_chunk(curve, l, best[1])
     return table
 
 
